@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Threshold-query throughput on the large dense workload.
+
+Workload: N = 256 bitmaps of r = 2^26 rows (2 GiB resident in HBM), bitmap k
+of density max(0.5/k, 1e-4) with its ones in geometric runs (mean 8); one
+step runs the four queries theta = 2, 128, 255 and the interval [2, 10].
+Metric: input GB/s = sum over queries of (N * r/8 + r/8) bytes / step time.
+Inputs (2.15 GB per query) exceed the 129 MB L2, so no flush is needed
+between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs the same workload on its own GPU (independent
+queries, weak scaling); the step time is the maximum over ranks.  The
+``reference`` arm times the CPU oracle on the host cores on a bounded sample
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+R_BITS = 1 << 26
+N = 256
+WORKLOAD = "large dense: N=256 bitmaps x r=2^26 rows, densities max(0.5/k,1e-4) in geometric runs; " \
+           "queries theta=2,128,255 and interval [2,10]"
+METRIC = "threshold-query input GB/s"
+DENSE_SOURCES = ["paper_1402_4073_gb300/csrc/bm_dense.cu", "paper_1402_4073_gb300/csrc/bm_device.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dense_csa_n256_r2e26.txt")
+
+
+def query_bytes(n: int, r_bits: int) -> int:
+    """Algorithmic bytes of one query: n inputs read plus one output written."""
+    return n * r_bits // 8 + r_bits // 8
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sources_sha() -> str:
+    h = hashlib.sha256()
+    for s in DENSE_SOURCES:
+        h.update(open(os.path.join(ROOT, s), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch():
+    """dram bytes per dense launch from the committed ncu summary, if it was
+    taken on the current kernel sources."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    kv = {}
+    for line in open(TRAFFIC_FILE):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha256_16") != sources_sha():
+        return None
+    try:
+        return int(float(kv["dram_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.device), "-lms", "50", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_setup(backend: str):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def cpu_sample_time(words, queries, r_bits, budget_s: float):
+    """Time the oracle on a bounded prefix of words, grown until it takes
+    about budget_s seconds; returns (bytes per second, sample words, threads)."""
+    import oracle
+    nw = 256
+    while True:
+        t0 = time.perf_counter()
+        for q in queries:
+            oracle.query(words, q, r_bits, 0, nw)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or nw >= words.shape[1]:
+            break
+        nw = min(words.shape[1], nw * 4)
+    rows = 64 * nw
+    nbytes = sum(query_bytes(q.n, rows) for q in queries)
+    return nbytes / dt, nw, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup("gloo")
+    if rank != 0:
+        return
+    import datagen
+    import oracle
+    oracle.build()
+    datagen.build()
+    words, queries = datagen.config2(R_BITS, N)
+    cores = os.cpu_count() or 1
+    # one step = the four queries over a fixed prefix of words, sized to ~1 s
+    _, nw, dt = cpu_sample_time(words, queries, R_BITS, 2.0)
+    nw = max(64, int(nw * min(8.0, 1.0 / max(dt, 1e-3))))
+    nw = min(nw, words.shape[1])
+    for _ in range(args.warmup):
+        for q in queries:
+            oracle.query(words, q, R_BITS, 0, nw)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for q in queries:
+            oracle.query(words, q, R_BITS, 0, nw)
+    el = time.perf_counter() - t0
+    step_bytes = sum(query_bytes(q.n, 64 * nw) for q in queries)
+    value = step_bytes * args.steps / el / 1e9
+    sample = f"first {nw} of {words.shape[1]} words ({64 * nw} rows) of each of the 4 queries per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * el / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "r_bits": R_BITS, "queries_per_step": 4},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0,
+                    help="seconds of oracle work for the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.cuda_build_module().build()
+    import datagen
+    import paper_1402_4073_gb300 as bm
+    datagen.build()
+
+    words, queries = datagen.config2(R_BITS, N)
+    pool = bm.Pool(R_BITS, N, device=local)
+    pool.put_dense(words)
+    stream = torch.cuda.current_stream()
+    outs = [pool.empty_words() for _ in queries]
+    cards = torch.zeros(len(queries), dtype=torch.int64, device="cuda")
+    tables = {i: bm.interval_table(q.n, q.lo, q.hi) for i, q in enumerate(queries) if q.kind == 1}
+
+    def launch(i, q, out=None):
+        o = outs[i] if out is None else out
+        if q.kind == 0:
+            bm.threshold(pool, q.ids, q.theta, o, cards[i:i + 1])
+        else:
+            bm.symmetric(pool, q.ids, tables[i], o, cards[i:i + 1])
+
+    # pick the dense feeding variant by timing a few candidates (results are identical)
+    candidates = [(1, 128, 4, 1), (1, 128, 3, 1), (1, 64, 6, 2), (1, 64, 4, 3), (0, 256, 4, 2),
+                  (0, 256, 4, 3)]
+    best, best_t = None, 1e30
+    for c in candidates:
+        pool.set_dense_config(*c)
+        for _ in range(2):
+            launch(0, queries[0])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            launch(0, queries[0])
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        if t < best_t:
+            best, best_t = c, t
+    pool.set_dense_config(*best)
+    pool.status()
+
+    for _ in range(args.warmup):
+        for i, q in enumerate(queries):
+            launch(i, q)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    # keep the GPU busy while the sampler starts
+    for _ in range(20):
+        for i, q in enumerate(queries):
+            launch(i, q)
+    nq = len(queries)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * nq)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for s in range(args.steps):
+        for i, q in enumerate(queries):
+            ev[s][2 * i].record(stream)
+            launch(i, q)
+            ev[s][2 * i + 1].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    pool.status()
+    el_ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([el_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        el_ms = float(t.item())
+    step_bytes = sum(query_bytes(q.n, R_BITS) for q in queries)
+    value = step_bytes * args.steps * world / (el_ms / 1e3) / 1e9
+    launch_ms = [ev[s][2 * i].elapsed_time(ev[s][2 * i + 1]) for s in range(args.steps)
+                 for i in range(nq)]
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    achieved = query_bytes(N, R_BITS) / avg_launch_s / 1e9
+    peak, peak_src = peaks()
+
+    # end to end through the public API: host ids in, output bitmap and
+    # cardinality copied back to pinned host memory every step
+    host_out = [torch.empty(pool.words, dtype=torch.int64, pin_memory=True) for _ in queries]
+    host_card = torch.empty(nq, dtype=torch.int64, pin_memory=True)
+    e2e_steps = max(3, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i, q in enumerate(queries):
+            launch(i, q)
+            host_out[i].copy_(outs[i], non_blocking=True)
+        host_card.copy_(cards, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = sum(4 * q.n + (8 * len(tables[i]) if i in tables else 0) for i, q in enumerate(queries))
+    d2h = nq * pool.words * 8 + nq * 8
+    e2e = step_bytes * world / e2e_s / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        bps, nw, dt = cpu_sample_time(words, queries, R_BITS, args.cpu_budget)
+        cpu = {"value": round(bps / 1e9, 4), "unit": "GB/s", "cores": os.cpu_count() or 1,
+               "kind": "oracle",
+               "sample": f"the 4 queries over the first {nw} of {words.shape[1]} words "
+                         f"({64 * nw} rows), {dt:.1f} s"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(el_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "r_bits": R_BITS, "queries_per_step": nq,
+                       "queries_per_s": round(nq * args.steps * world / (el_ms / 1e3), 1),
+                       "l2": "inputs (2.15 GB per query) larger than L2; no flush",
+                       "dense_config": list(best)},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "peak_source": f"hbm_gbs of {peak_src}",
+                         "traffic": traffic_per_launch(),
+                         "kernel": "csa dense (bit-sliced carry-save counter)",
+                         "algorithmic_bytes_per_launch": query_bytes(N, R_BITS)},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": nq * args.steps,
+            "clocks": clocks,
+        }))
+    pool.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

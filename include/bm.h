@@ -1,0 +1,186 @@
+/*
+ * bm.h — C ABI of the GB300 threshold / symmetric-function query library.
+ *
+ * What is computed (Kaser and Lemire, "Threshold and Symmetric Functions over
+ * Bitmaps", Sec. 1 "Formulation", Sec. 2.2 and 2.3): given N bitmaps
+ * B_1..B_N of r bits and a threshold theta, the output bitmap has bit i set
+ * iff c_i = |{k : bit i of B_k is set}| >= theta (the threshold function
+ * T(theta, .)); for a symmetric function f given by its truth table over the
+ * counts 0..N, bit i is set iff f(c_i) = 1.  The cardinality is the number of
+ * ones of the output bitmap.
+ *
+ * Conventions shared by every entry point:
+ *  - Bit layout (Sec. 2.1, "Uncompressed Bitmaps"): row i is bit (i mod 64)
+ *    of 64-bit word i / 64, least significant bit first; a bitmap of r rows
+ *    has ceil(r / 64) words.  Output bits at rows >= r are always written 0;
+ *    input bits at rows >= r are ignored.
+ *  - A repeated id counts once per repeat (integer weights by replication,
+ *    Sec. 2.3).  theta = 0 selects every row; theta > N selects none; theta = 1
+ *    is the union (wide OR) and theta = N the intersection (wide AND).
+ *  - Streams: every query entry point is asynchronous on `stream` (a
+ *    cudaStream_t passed as void*; NULL is the legacy default stream).
+ *    Host arrays (ids, truth tables, query descriptors) are copied before the
+ *    call returns and may be reused at once.  Device outputs are valid once
+ *    the stream reaches the point of the call.
+ *  - Ownership: the pool owns its device bitmaps; the caller owns output
+ *    buffers (device memory it allocated, e.g. a torch tensor).
+ *  - Errors: 0 is success; negative values are the BM_E* codes below and
+ *    leave outputs untouched unless stated.  Device-side bounded waits that
+ *    expire are reported by bm_pool_status().
+ *  - Thread safety: calls on one pool are serialised by an internal mutex.
+ */
+#ifndef BM_H
+#define BM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BM_OK 0
+#define BM_EINVAL (-1)    /* bad argument: NULL pointer, n = 0, n > BM_N_MAX, bad kind ... */
+#define BM_ERANGE (-2)    /* id >= capacity, id not loaded, position >= r or unsorted */
+#define BM_ENOMEM (-3)    /* device or pinned allocation failed, or the pool budget is exceeded */
+#define BM_ECUDA (-4)     /* a CUDA runtime call failed */
+#define BM_ETIMEOUT (-5)  /* a bounded device-side wait expired */
+#define BM_EBUSY (-6)     /* admission refused (server memory budget or slot table full) */
+#define BM_ENOTREADY (-7) /* a result is not complete yet */
+
+/* Largest number of inputs of one query (counts then fit 16 bits). */
+#define BM_N_MAX 65535u
+
+typedef struct bm_pool bm_pool;
+
+/* ------------------------------------------------------------------------
+ * Bitmap pool: a device-resident set of `capacity` bitmaps of r rows.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Create a pool on CUDA device `device` for `capacity` bitmaps of `r_bits`
+ * rows (1 <= r_bits <= 2^32).  Dense storage is one device allocation with
+ * each bitmap padded to a multiple of 32 words (256 bytes), zero-filled.
+ * `mem_budget` bounds the pool's total device bytes (dense storage, position
+ * lists, their tile index and staging); 0 means no bound.  The paper keeps
+ * the N bitmaps of a query in memory (Sec. 1, after the complexity tables);
+ * the pool is that memory, resident in HBM.
+ * Returns BM_ENOMEM if the dense storage alone exceeds the budget or cannot
+ * be allocated.  *out receives the pool.
+ */
+int bm_pool_create(int device, uint64_t r_bits, uint32_t capacity, uint64_t mem_budget,
+                   bm_pool** out);
+
+/* Free every device and pinned allocation of the pool.  NULL is accepted. */
+int bm_pool_destroy(bm_pool* pool);
+
+/*
+ * Load `count` dense bitmaps into ids first_id .. first_id + count - 1.
+ * Bitmap j is read from words + j * src_stride_words (ceil(r/64) words);
+ * `words` is a device pointer if words_on_device != 0, else host memory.
+ * Input bits at rows >= r are cleared in the pool copy.  The per-bitmap
+ * cardinality is computed on the device and kept on the host for the
+ * selector's density features.  Synchronous.
+ * Errors: BM_ERANGE if the id range exceeds capacity.
+ */
+int bm_pool_put_dense(bm_pool* pool, uint32_t first_id, uint32_t count, const uint64_t* words,
+                      uint64_t src_stride_words, int words_on_device);
+
+/*
+ * Load sorted position lists (the "sorted integer list" form of a set,
+ * Sec. 1 and 4.2) for ids first_id .. first_id + count - 1.  List j is
+ * positions[offsets[j] .. offsets[j+1]) (offsets are host uint64, count + 1
+ * entries, relative to `positions`); `positions` is device memory if
+ * positions_on_device != 0, else host memory.  Lists must be strictly
+ * increasing and every position < r (checked on the host for host input,
+ * by a device check kernel for device input; BM_ERANGE otherwise).  A
+ * per-list tile index (first list entry at each multiple of 8192 rows) is
+ * built on the device.  Synchronous.  A list loaded for an id replaces any
+ * earlier list of that id.
+ */
+int bm_pool_put_positions(bm_pool* pool, uint32_t first_id, uint32_t count,
+                          const uint32_t* positions, const uint64_t* offsets,
+                          int positions_on_device);
+
+typedef struct bm_pool_info_t {
+    uint64_t r_bits;           /* rows per bitmap */
+    uint64_t words;            /* ceil(r / 64) */
+    uint64_t stride_words;     /* words between consecutive bitmaps in dense storage */
+    uint32_t capacity;         /* number of ids */
+    uint32_t dense_loaded;     /* ids holding a dense bitmap */
+    uint32_t lists_loaded;     /* ids holding a position list */
+    uint32_t sm_count;         /* streaming multiprocessors of the pool's device */
+    uint64_t device_bytes;     /* device bytes held by the pool */
+    const uint64_t* dense_base;/* device address of id 0's dense words */
+} bm_pool_info_t;
+
+/* Fill *out with the pool's shape. */
+int bm_pool_info(const bm_pool* pool, bm_pool_info_t* out);
+
+/*
+ * Host-side cardinality of bitmap `id` (from its dense load, else its
+ * position list length).  BM_ERANGE if the id holds neither.
+ */
+int bm_pool_bitmap_cardinality(const bm_pool* pool, uint32_t id, uint64_t* out);
+
+/*
+ * Synchronise the pool's device and report device-side failures since the
+ * previous call: BM_ETIMEOUT if a kernel's bounded wait expired (its outputs
+ * are then undefined), else BM_OK.  Clears the flag.
+ */
+int bm_pool_status(bm_pool* pool);
+
+/*
+ * Choose how the pool's dense kernel feeds its inputs (the autotuner sets
+ * this; results are identical for every choice).
+ *   variant 0: direct 128-bit streaming loads; `threads` ignored (256).
+ *   variant 1: bulk-copy (TMA) pipeline through shared memory with
+ *              `threads` consumer threads per CTA (64 or 128) and `stages`
+ *              pipeline stages (2..8) of 16 bitmaps each.
+ * ctas_per_sm (1..8) caps the persistent grid at ctas_per_sm x SM count.
+ * BM_EINVAL for values outside these ranges.
+ */
+int bm_pool_set_dense_config(bm_pool* pool, int variant, int threads, int stages,
+                             int ctas_per_sm);
+
+/* ------------------------------------------------------------------------
+ * Single queries
+ * ---------------------------------------------------------------------- */
+
+/*
+ * Threshold query T(theta, {B_ids[0], ..., B_ids[n-1]}) (Sec. 2.3).
+ * ids: host array of n pool ids (1 <= n <= BM_N_MAX, repeats allowed).
+ * out_words: device, ceil(r/64) words, written in full.
+ * out_card: device uint64, receives the output's cardinality (may be NULL).
+ * Runs the dense bit-sliced carry-save counter over the pool's dense words.
+ * Errors: BM_EINVAL (NULL ids/out_words, n = 0 or > BM_N_MAX), BM_ERANGE (an
+ * id >= capacity or without a dense bitmap), BM_ECUDA (launch failure).
+ */
+int bm_threshold(bm_pool* pool, const uint32_t* ids, uint32_t n, uint32_t theta,
+                 uint64_t* out_words, uint64_t* out_card, void* stream);
+
+/*
+ * Symmetric-function query (Sec. 2.2; counter-based form in Sec. 4.2):
+ * output bit i = f(c_i) with f given by `table`, a host array of
+ * ceil((n + 1) / 64) uint64 words whose bit c (word c / 64, bit c mod 64) is
+ * f(c) for c = 0..n; bits above n are ignored.  Other arguments and errors
+ * as bm_threshold.
+ */
+int bm_symmetric(bm_pool* pool, const uint32_t* ids, uint32_t n, const uint64_t* table,
+                 uint64_t* out_words, uint64_t* out_card, void* stream);
+
+/*
+ * Number of ones among the first r_bits rows of a device bitmap `words`
+ * (ceil(r/64) words), written to the device uint64 *out_card (Sec. 2.1: the
+ * cardinality of the set a bitmap stores).  Asynchronous on `stream`.
+ */
+int bm_cardinality(const uint64_t* words, uint64_t r_bits, uint64_t* out_card, void* stream);
+
+/* Static text for a status code. */
+const char* bm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BM_H */

@@ -1,0 +1,189 @@
+"""GB300-native threshold and symmetric-function queries over bitmaps.
+
+Python binding of ``libbm.so`` (C ABI in ``include/bm.h``).  The binding only
+marshals arguments: host arrays become pointers, torch CUDA tensors become
+device pointers, and the current torch stream becomes the launch stream.
+Device memory for outputs comes from PyTorch's allocator.
+
+Bit layout: row i of a bitmap is bit i % 64 of 64-bit word i // 64.  Word
+arrays are numpy ``uint64`` on the host and torch ``int64`` tensors (same
+bits) on the device.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch  # loads the CUDA runtime that libbm.so then shares
+
+from . import _native
+
+lib = _native.load()
+
+BM_OK, BM_EINVAL, BM_ERANGE, BM_ENOMEM, BM_ECUDA, BM_ETIMEOUT, BM_EBUSY, BM_ENOTREADY = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+BM_N_MAX = 65535
+
+
+class BMError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = lib.bm_strerror(code).decode()
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+def check(rc: int, what: str = "") -> None:
+    if rc != BM_OK:
+        raise BMError(rc, what)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _host_u32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+
+
+def _host_u64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint64))
+
+
+def _dev_ptr(t: torch.Tensor | None, min_bytes: int = 0) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if t.numel() * t.element_size() < min_bytes:
+        raise ValueError(f"device buffer too small: need {min_bytes} bytes")
+    return t.data_ptr()
+
+
+def words_for(r_bits: int) -> int:
+    return (r_bits + 63) // 64
+
+
+class Pool:
+    """A device-resident pool of `capacity` bitmaps of `r_bits` rows."""
+
+    def __init__(self, r_bits: int, capacity: int, device: int = 0, mem_budget: int = 0):
+        h = ctypes.c_void_p()
+        check(lib.bm_pool_create(device, r_bits, capacity, mem_budget, ctypes.byref(h)),
+              "bm_pool_create")
+        self.handle = h
+        self.r_bits = r_bits
+        self.capacity = capacity
+        self.device = device
+        self.words = words_for(r_bits)
+
+    def close(self):
+        if self.handle:
+            lib.bm_pool_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def put_dense(self, words, first_id: int = 0):
+        """Load bitmaps (rows of a 2-D uint64 numpy array or int64 CUDA tensor)."""
+        if isinstance(words, torch.Tensor):
+            if words.dim() == 1:
+                words = words.view(1, -1)
+            if words.stride(1) != 1:
+                raise ValueError("rows must be contiguous")
+            check(lib.bm_pool_put_dense(self.handle, first_id, words.shape[0], words.data_ptr(),
+                                        words.stride(0), 1 if words.is_cuda else 0),
+                  "bm_pool_put_dense")
+            return
+        w = _host_u64(words)
+        if w.ndim == 1:
+            w = w.reshape(1, -1)
+        check(lib.bm_pool_put_dense(self.handle, first_id, w.shape[0], w.ctypes.data, w.shape[1], 0),
+              "bm_pool_put_dense")
+
+    def put_positions(self, flat, offsets, first_id: int = 0):
+        """Load sorted position lists: list j is flat[offsets[j]:offsets[j+1]]."""
+        offs = _host_u64(offsets)
+        if isinstance(flat, torch.Tensor):
+            check(lib.bm_pool_put_positions(self.handle, first_id, len(offs) - 1, flat.data_ptr(),
+                                            offs.ctypes.data, 1 if flat.is_cuda else 0),
+                  "bm_pool_put_positions")
+            return
+        f = _host_u32(flat)
+        fp = f.ctypes.data if len(f) else None
+        check(lib.bm_pool_put_positions(self.handle, first_id, len(offs) - 1, fp, offs.ctypes.data, 0),
+              "bm_pool_put_positions")
+
+    def info(self) -> dict:
+        i = _native.bm_pool_info_t()
+        check(lib.bm_pool_info(self.handle, ctypes.byref(i)), "bm_pool_info")
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def bitmap_cardinality(self, id_: int) -> int:
+        c = ctypes.c_uint64()
+        check(lib.bm_pool_bitmap_cardinality(self.handle, id_, ctypes.byref(c)))
+        return int(c.value)
+
+    def status(self) -> None:
+        """Synchronise; raise BMError(BM_ETIMEOUT) if a device wait expired."""
+        check(lib.bm_pool_status(self.handle), "bm_pool_status")
+
+    def set_dense_config(self, variant: int, threads: int = 128, stages: int = 4,
+                         ctas_per_sm: int = 1) -> None:
+        check(lib.bm_pool_set_dense_config(self.handle, variant, threads, stages, ctas_per_sm),
+              "bm_pool_set_dense_config")
+
+    def empty_words(self, n: int | None = None) -> torch.Tensor:
+        shape = (self.words,) if n is None else (n, self.words)
+        return torch.empty(shape, dtype=torch.int64, device=f"cuda:{self.device}")
+
+
+def threshold(pool: Pool, ids, theta: int, out_words: torch.Tensor,
+              out_card: torch.Tensor | None = None, stream=None) -> None:
+    """T(theta) over pool bitmaps `ids` into `out_words` (+ cardinality)."""
+    i = _host_u32(ids)
+    check(lib.bm_threshold(pool.handle, i.ctypes.data, len(i), int(theta),
+                           _dev_ptr(out_words, 8 * pool.words), _dev_ptr(out_card, 8), _stream(stream)),
+          "bm_threshold")
+
+
+def symmetric(pool: Pool, ids, table, out_words: torch.Tensor,
+              out_card: torch.Tensor | None = None, stream=None) -> None:
+    """Symmetric function with truth table `table` (uint64 words, bit c = f(c))."""
+    i = _host_u32(ids)
+    t = _host_u64(table)
+    if t.size * 64 < len(i) + 1:
+        raise ValueError("truth table needs n + 1 bits")
+    check(lib.bm_symmetric(pool.handle, i.ctypes.data, len(i), t.ctypes.data,
+                           _dev_ptr(out_words, 8 * pool.words), _dev_ptr(out_card, 8), _stream(stream)),
+          "bm_symmetric")
+
+
+def cardinality(words: torch.Tensor, r_bits: int, out_card: torch.Tensor, stream=None) -> None:
+    check(lib.bm_cardinality(_dev_ptr(words, 8 * words_for(r_bits)), r_bits, _dev_ptr(out_card, 8),
+                             _stream(stream)), "bm_cardinality")
+
+
+def interval_table(n: int, lo: int, hi: int) -> np.ndarray:
+    """Truth table words of f(c) = [lo <= c <= hi], c = 0..n (argument marshalling)."""
+    t = np.zeros((n + 1 + 63) // 64, dtype=np.uint64)
+    for c in range(max(lo, 0), min(hi, n) + 1):
+        t[c // 64] |= np.uint64(1) << np.uint64(c % 64)
+    return t
+
+
+def to_numpy_words(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint64)

@@ -1,0 +1,65 @@
+"""ctypes loader for ``libbm.so``: argument marshalling only.
+
+Every computation happens in the library's CUDA kernels.  If the library is
+missing this module raises at import time; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbm.so")
+HEADERS = [os.path.join(os.path.dirname(HERE), "include", "bm.h")]
+
+u64, u32, i32, vp, dbl = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+P64 = ctypes.POINTER(ctypes.c_uint64)
+
+
+class bm_pool_info_t(ctypes.Structure):
+    _fields_ = [("r_bits", u64), ("words", u64), ("stride_words", u64), ("capacity", u32),
+                ("dense_loaded", u32), ("lists_loaded", u32), ("sm_count", u32),
+                ("device_bytes", u64), ("dense_base", vp)]
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "bm_strerror": (ctypes.c_char_p, [i32]),
+    "bm_pool_create": (i32, [i32, u64, u32, u64, ctypes.POINTER(vp)]),
+    "bm_pool_destroy": (i32, [vp]),
+    "bm_pool_put_dense": (i32, [vp, u32, u32, vp, u64, i32]),
+    "bm_pool_put_positions": (i32, [vp, u32, u32, vp, vp, i32]),
+    "bm_pool_info": (i32, [vp, ctypes.POINTER(bm_pool_info_t)]),
+    "bm_pool_bitmap_cardinality": (i32, [vp, u32, P64]),
+    "bm_pool_status": (i32, [vp]),
+    "bm_pool_set_dense_config": (i32, [vp, i32, i32, i32, i32]),
+    "bm_threshold": (i32, [vp, vp, u32, u32, vp, vp, vp]),
+    "bm_symmetric": (i32, [vp, vp, u32, vp, vp, vp, vp]),
+    "bm_cardinality": (i32, [vp, u64, vp, vp]),
+}
+
+
+def declared_symbols() -> list[str]:
+    """Entry points declared in include/*.h (function prototypes only)."""
+    names = []
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(bm_[a-z0-9_]+)\s*\(", src):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: the CUDA library must be built first "
+            "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+    lib = ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib

@@ -1,0 +1,118 @@
+// Single-query entry points: host validation, predicate compilation,
+// staging of ids and truth tables, dense kernel launch.
+#include <algorithm>
+#include <cstring>
+
+#include "bm_device.cuh"
+
+namespace bm {
+
+void threshold_truth(uint32_t n, uint32_t theta, std::vector<uint8_t>& f) {
+    f.assign((size_t)n + 1, 0);
+    for (uint32_t c = 0; c <= n; ++c) f[c] = c >= theta;
+}
+
+void interval_truth(uint32_t n, uint32_t lo, uint32_t hi, std::vector<uint8_t>& f) {
+    f.assign((size_t)n + 1, 0);
+    for (uint32_t c = 0; c <= n; ++c) f[c] = c >= lo && c <= hi;
+}
+
+Pred compile_pred(const uint8_t* f, uint32_t n) {
+    Pred p{};
+    p.v0 = f[0] ? 1u : 0u;
+    uint32_t m = 0;
+    for (uint32_t c = 1; c <= n; ++c)
+        if ((f[c] != 0) != (f[c - 1] != 0)) ++m;
+    if (m == 0) {
+        p.mode = 0;
+        return p;
+    }
+    if (m <= (uint32_t)kMaxTransitions) {
+        p.mode = 1;
+        for (uint32_t c = 1; c <= n; ++c)
+            if ((f[c] != 0) != (f[c - 1] != 0)) p.trans[p.ntrans++] = c;
+        return p;
+    }
+    p.mode = 2;
+    p.table_words32 = (n + 1 + 31) / 32;
+    return p;
+}
+
+}  // namespace bm
+
+using namespace bm;
+
+namespace {
+
+int validate_ids(const bm_pool* p, const uint32_t* ids, uint32_t n) {
+    if (!ids || n == 0 || n > BM_N_MAX) return BM_EINVAL;
+    for (uint32_t k = 0; k < n; ++k)
+        if (ids[k] >= p->capacity || !p->dense_present[ids[k]]) return BM_ERANGE;
+    return BM_OK;
+}
+
+// Stage ids (and a mode-2 table) and launch the dense kernel.
+int run_dense(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<uint8_t>& f,
+              uint64_t* out_words, uint64_t* out_card, cudaStream_t s) {
+    Pred pred = compile_pred(f.data(), n);
+    const size_t ids_bytes = ((size_t)n * 4 + 15) & ~(size_t)15;
+    const size_t tab_bytes = pred.mode == 2 ? (size_t)pred.table_words32 * 4 : 0;
+    bm_stage_slot* sl = nullptr;
+    int rc = stage_acquire(p, ids_bytes + tab_bytes, &sl);
+    if (rc) return rc;
+    memcpy(sl->h, ids, (size_t)n * 4);
+    if (tab_bytes) {
+        uint32_t* t = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(sl->h) + ids_bytes);
+        memset(t, 0, tab_bytes);
+        for (uint32_t c = 0; c <= n; ++c)
+            if (f[c]) t[c >> 5] |= 1u << (c & 31);
+        pred.table = reinterpret_cast<const uint32_t*>(static_cast<uint8_t*>(sl->d) + ids_bytes);
+    }
+    rc = stage_commit(sl, ids_bytes + tab_bytes, s);
+    if (rc) return rc;
+    if (out_card) BM_CUDA_TRY(cudaMemsetAsync(out_card, 0, 8, s));
+    DenseArgs a{};
+    a.base = p->d_dense;
+    a.stride_words = p->stride_words;
+    a.words = p->words;
+    a.r_bits = p->r_bits;
+    a.ids = static_cast<const uint32_t*>(sl->d);
+    a.n = n;
+    a.pred = pred;
+    a.out = out_words;
+    a.card = reinterpret_cast<unsigned long long*>(out_card);
+    a.err = p->d_err;
+    rc = launch_dense(a, p->dense_cfg, p->sm_count, s);
+    int rc2 = stage_release(sl, s);
+    return rc ? rc : rc2;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bm_threshold(bm_pool* p, const uint32_t* ids, uint32_t n, uint32_t theta,
+                 uint64_t* out_words, uint64_t* out_card, void* stream) {
+    if (!p || !out_words) return BM_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    int rc = validate_ids(p, ids, n);
+    if (rc) return rc;
+    BM_CUDA_TRY(cudaSetDevice(p->device));
+    std::vector<uint8_t> f;
+    threshold_truth(n, theta, f);
+    return run_dense(p, ids, n, f, out_words, out_card, static_cast<cudaStream_t>(stream));
+}
+
+int bm_symmetric(bm_pool* p, const uint32_t* ids, uint32_t n, const uint64_t* table,
+                 uint64_t* out_words, uint64_t* out_card, void* stream) {
+    if (!p || !out_words || !table) return BM_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    int rc = validate_ids(p, ids, n);
+    if (rc) return rc;
+    BM_CUDA_TRY(cudaSetDevice(p->device));
+    std::vector<uint8_t> f((size_t)n + 1);
+    for (uint32_t c = 0; c <= n; ++c) f[c] = (uint8_t)((table[c >> 6] >> (c & 63)) & 1u);
+    return run_dense(p, ids, n, f, out_words, out_card, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,340 @@
+// Dense bit-sliced carry-save counter (the adder-circuit family of Sec. 4.3
+// evaluated word-parallel, 32 rows per register), its predicate and the
+// output/cardinality epilogue.
+//
+// Each thread owns a column of 128 rows (one 16-byte slice: two 64-bit
+// words, four 32-bit lanes) of every input bitmap and streams the N inputs of
+// that column through K counter planes held in registers.  Sixteen inputs
+// at a time go through a 15-full-adder sideways-sum tree (one LOP3 for each
+// sum and each carry).  After the last input the predicate (threshold
+// comparator, interval, or table lookup) turns the planes into the output
+// slice, which is stored and popcounted.
+//
+// Two ways of feeding the inputs:
+//  * variant 0 ("direct"): each thread issues 16 streaming 128-bit loads per
+//    step, coalesced across the warp (consecutive threads read consecutive
+//    16-byte slices of the same bitmap).
+//  * variant 1 ("bulk"): one producer thread per CTA moves each
+//    (tile, group of 16 bitmaps) into a shared-memory stage with bulk copies
+//    (cp.async.bulk, the non-tensor TMA form) completing on an mbarrier; the
+//    consumer warps read 128-bit slices from shared memory.  Stages are
+//    recycled through a second mbarrier per stage.  All waits are bounded.
+#include <algorithm>
+
+#include "bm_device.cuh"
+
+namespace bm {
+
+int planes_for(uint32_t n) {
+    int k = 0;
+    while ((1ull << k) <= n) ++k;  // counts 0..n need k bits
+    return k;
+}
+
+namespace {
+
+using namespace dev;
+
+// Per-lane accumulation of a partial group (nb < 16 inputs) read by `get(b)`.
+template <int K, typename Get>
+__device__ __forceinline__ void add_partial(uint32_t (&P)[4][K], uint32_t nb, Get get) {
+    uint32_t b = 0;
+    for (; b + 2 <= nb; b += 2) {
+        uint4 u = get(b), v = get(b + 1);
+        add2<K>(P[0], u.x, v.x);
+        add2<K>(P[1], u.y, v.y);
+        add2<K>(P[2], u.z, v.z);
+        add2<K>(P[3], u.w, v.w);
+    }
+    if (b < nb) {
+        uint4 u = get(b);
+        add1<K>(P[0], u.x);
+        add1<K>(P[1], u.y);
+        add1<K>(P[2], u.z);
+        add1<K>(P[3], u.w);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void add_group16(uint32_t (&P)[4][K], const uint4 (&v)[16]) {
+    uint32_t x[16];
+#pragma unroll
+    for (int b = 0; b < 16; ++b) x[b] = v[b].x;
+    add16<K>(P[0], x);
+#pragma unroll
+    for (int b = 0; b < 16; ++b) x[b] = v[b].y;
+    add16<K>(P[1], x);
+#pragma unroll
+    for (int b = 0; b < 16; ++b) x[b] = v[b].z;
+    add16<K>(P[2], x);
+#pragma unroll
+    for (int b = 0; b < 16; ++b) x[b] = v[b].w;
+    add16<K>(P[3], x);
+}
+
+// Predicate, tail mask, store and popcount of one 128-row column.
+template <int K>
+__device__ __forceinline__ uint32_t finish_column(const uint32_t (&P)[4][K], const DenseArgs& a,
+                                                  const uint32_t* tab, uint64_t col, bool vec_ok) {
+    uint32_t o0 = eval_pred<K>(P[0], a.pred, tab);
+    uint32_t o1 = eval_pred<K>(P[1], a.pred, tab);
+    uint32_t o2 = eval_pred<K>(P[2], a.pred, tab);
+    uint32_t o3 = eval_pred<K>(P[3], a.pred, tab);
+    uint64_t w0 = (uint64_t)o0 | ((uint64_t)o1 << 32);
+    uint64_t w1 = (uint64_t)o2 | ((uint64_t)o3 << 32);
+    const uint64_t i0 = 2 * col, i1 = i0 + 1;
+    const uint32_t tail = (uint32_t)(a.r_bits & 63u);
+    const uint64_t last = a.words - 1;
+    if (tail) {
+        const uint64_t m = (1ull << tail) - 1ull;
+        if (i0 == last) w0 &= m;
+        if (i1 == last) w1 &= m;
+    }
+    if (i1 < a.words) {
+        if (vec_ok) {
+            asm volatile("st.global.v2.u64 [%0], {%1, %2};" ::"l"(a.out + i0), "l"(w0), "l"(w1)
+                         : "memory");
+        } else {
+            a.out[i0] = w0;
+            a.out[i1] = w1;
+        }
+        return (uint32_t)(__popcll(w0) + __popcll(w1));
+    }
+    if (i0 < a.words) {
+        a.out[i0] = w0;
+        return (uint32_t)__popcll(w0);
+    }
+    return 0;
+}
+
+__device__ __forceinline__ void flush_card(unsigned long long card, unsigned long long* out) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) card += __shfl_xor_sync(0xFFFFFFFFu, card, o);
+    if ((threadIdx.x & 31) == 0 && out && card) atomicAdd(out, card);
+}
+
+__device__ __forceinline__ void load_table(const DenseArgs& a, uint32_t* tab, int tid, int nthr) {
+    if (a.pred.mode == 2)
+        for (uint32_t i = tid; i < a.pred.table_words32; i += nthr) tab[i] = a.pred.table[i];
+}
+
+// ---------------------------------------------------------------------------
+// variant 0: direct streaming loads
+
+template <int K>
+__global__ void __launch_bounds__(256, (K <= 13 ? 2 : 1)) csa_direct_kernel(DenseArgs a) {
+    extern __shared__ uint32_t tab[];
+    load_table(a, tab, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const uint64_t ncols = (a.words + 1) / 2;
+    const bool vec_ok = ((reinterpret_cast<uintptr_t>(a.out) & 15u) == 0);
+    unsigned long long card = 0;
+    for (uint64_t col = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; col < ncols;
+         col += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t P[4][K];
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+#pragma unroll
+            for (int j = 0; j < K; ++j) P[l][j] = 0u;
+        const uint64_t* colbase = a.base + 2 * col;
+        uint32_t k = 0;
+        for (; k + 16 <= a.n; k += 16) {
+            uint4 v[16];
+#pragma unroll
+            for (int b = 0; b < 16; ++b)
+                v[b] = ld_stream(colbase + (uint64_t)__ldg(a.ids + k + b) * a.stride_words);
+            add_group16<K>(P, v);
+        }
+        if (k < a.n) {
+            const uint32_t* ids = a.ids + k;
+            add_partial<K>(P, a.n - k, [&](uint32_t b) {
+                return ld_stream(colbase + (uint64_t)__ldg(ids + b) * a.stride_words);
+            });
+        }
+        card += finish_column<K>(P, a, tab, col, vec_ok);
+    }
+    flush_card(card, a.card);
+}
+
+// ---------------------------------------------------------------------------
+// variant 1: bulk-copy pipeline through shared memory
+
+template <int K, int NT>
+__global__ void __launch_bounds__(NT + 32, 1) csa_bulk_kernel(DenseArgs a, int stages) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint4* buf = reinterpret_cast<uint4*>(smem);  // [stages][16][NT]
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)stages * 16 * NT * 16);
+    uint64_t* empty = full + stages;
+    uint32_t* tab = reinterpret_cast<uint32_t*>(empty + stages);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int kConsumerWarps = NT / 32;
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        fence_barrier_init();
+    }
+    load_table(a, tab, tid, blockDim.x);
+    __syncthreads();
+
+    const uint64_t ncols = (a.words + 1) / 2;
+    const uint64_t ntiles = (ncols + NT - 1) / NT;
+    const uint32_t ngroups = (a.n + 15) / 16;
+    const uint64_t stride_bytes = a.stride_words * 8;
+
+    if (warp == kConsumerWarps) {
+        // producer: one elected thread issues the bulk copies
+        if (lane != 0) return;
+        const uint64_t pol = policy_evict_first();
+        uint64_t it = 0;
+        bool ok = true;
+        for (uint64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const uint64_t off = tile * (uint64_t)NT * 16;
+            const uint32_t bytes = (uint32_t)min((uint64_t)NT * 16, stride_bytes - off);
+            for (uint32_t g = 0; g < ngroups; ++g, ++it) {
+                const int s = (int)(it % (uint64_t)stages);
+                if (it >= (uint64_t)stages &&
+                    !mbar_wait_bounded(&empty[s], (uint32_t)((it / stages - 1) & 1), a.err)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t nb = min(16u, a.n - g * 16);
+                mbar_arrive_expect_tx(&full[s], nb * bytes);
+                const uint32_t* ids = a.ids + g * 16;
+                for (uint32_t b = 0; b < nb; ++b) {
+                    const uint8_t* src = reinterpret_cast<const uint8_t*>(a.base) +
+                                         (uint64_t)__ldg(ids + b) * stride_bytes + off;
+                    bulk_g2s(buf + ((size_t)s * 16 + b) * NT, src, bytes, &full[s], pol);
+                }
+            }
+        }
+        // every issued copy must land before this CTA may exit
+        const uint64_t first = it > (uint64_t)stages ? it - stages : 0;
+        for (uint64_t j = first; j < it; ++j)
+            mbar_wait_bounded(&full[j % stages], (uint32_t)((j / stages) & 1), a.err);
+        return;
+    }
+
+    // consumers
+    const bool vec_ok = ((reinterpret_cast<uintptr_t>(a.out) & 15u) == 0);
+    unsigned long long card = 0;
+    uint64_t it = 0;
+    bool ok = true;
+    for (uint64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        uint32_t P[4][K];
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+#pragma unroll
+            for (int j = 0; j < K; ++j) P[l][j] = 0u;
+        for (uint32_t g = 0; g < ngroups; ++g, ++it) {
+            const int s = (int)(it % (uint64_t)stages);
+            // every lane waits; the warp proceeds only if all lanes saw the stage land
+            const bool landed = mbar_wait_bounded(&full[s], (uint32_t)((it / stages) & 1), a.err);
+            if (!__all_sync(0xFFFFFFFFu, landed)) {
+                ok = false;
+                break;
+            }
+            const uint4* st = buf + (size_t)s * 16 * NT + tid;
+            const uint32_t nb = min(16u, a.n - g * 16);
+            if (nb == 16) {
+                uint4 v[16];
+#pragma unroll
+                for (int b = 0; b < 16; ++b) v[b] = st[b * NT];
+                add_group16<K>(P, v);
+            } else {
+                add_partial<K>(P, nb, [&](uint32_t b) { return st[b * NT]; });
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+        if (!ok) break;
+        const uint64_t col = tile * NT + tid;
+        if (col < ncols) card += finish_column<K>(P, a, tab, col, vec_ok);
+    }
+    if (ok) flush_card(card, a.card);
+}
+
+template <int K>
+int launch_k(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStream_t s) {
+    const uint64_t ncols = (a.words + 1) / 2;
+    const size_t tab_bytes = a.pred.mode == 2 ? (size_t)a.pred.table_words32 * 4 : 0;
+    if (cfg.variant == 0) {
+        const int threads = 256;
+        const uint64_t blocks_needed = (ncols + threads - 1) / threads;
+        const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);
+        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(blocks_needed, cap));
+        auto fn = csa_direct_kernel<K>;
+        if (tab_bytes > 48 * 1024)
+            BM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tab_bytes));
+        fn<<<grid, threads, tab_bytes, s>>>(a);
+        BM_CUDA_TRY(cudaGetLastError());
+        return BM_OK;
+    }
+    int dev = 0, optin = 0;
+    BM_CUDA_TRY(cudaGetDevice(&dev));
+    BM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    auto run = [&](auto fn, int nt) -> int {
+        // stages of 16 bitmaps x nt 16-byte slices, plus two mbarriers each
+        const int fit = (int)(((size_t)optin - tab_bytes) / ((size_t)256 * nt + 16));
+        const int stages = std::max(2, std::min({8, cfg.stages, fit}));
+        if (fit < 2) return BM_EINVAL;
+        const size_t bytes = (size_t)stages * 16 * nt * 16 + 2 * (size_t)stages * 8 + tab_bytes;
+        BM_CUDA_TRY(
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        const uint64_t ntiles = (ncols + nt - 1) / nt;
+        const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);
+        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(ntiles, cap));
+        fn<<<grid, nt + 32, bytes, s>>>(a, stages);
+        BM_CUDA_TRY(cudaGetLastError());
+        return BM_OK;
+    };
+    if (cfg.threads <= 64) return run(csa_bulk_kernel<K, 64>, 64);
+    return run(csa_bulk_kernel<K, 128>, 128);
+}
+
+}  // namespace
+
+int launch_dense(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStream_t s) {
+    if (a.words == 0) return BM_OK;
+    const int k = planes_for(a.n);
+    if (k <= 5) return launch_k<5>(a, cfg, sm_count, s);
+    if (k <= 9) return launch_k<9>(a, cfg, sm_count, s);
+    if (k <= 13) return launch_k<13>(a, cfg, sm_count, s);
+    return launch_k<17>(a, cfg, sm_count, s);
+}
+
+// ---------------------------------------------------------------------------
+// cardinality of one bitmap (the paper's |B_i|, Sec. 2.1)
+
+namespace {
+__global__ void __launch_bounds__(256) cardinality_kernel(const uint64_t* w, uint64_t words,
+                                                          uint64_t r_bits,
+                                                          unsigned long long* out) {
+    unsigned long long c = 0;
+    const uint32_t tail = (uint32_t)(r_bits & 63u);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t x = w[i];
+        if (tail && i == words - 1) x &= (1ull << tail) - 1ull;
+        c += (unsigned long long)__popcll(x);
+    }
+    flush_card(c, out);
+}
+}  // namespace
+
+int launch_cardinality(const uint64_t* words, uint64_t r_bits, unsigned long long* out,
+                       int sm_count, cudaStream_t s) {
+    BM_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(unsigned long long), s));
+    const uint64_t nw = (r_bits + 63) / 64;
+    if (nw == 0) return BM_OK;
+    const uint64_t blocks = std::min<uint64_t>((nw + 255) / 256, (uint64_t)sm_count * 8);
+    cardinality_kernel<<<(unsigned)std::max<uint64_t>(1, blocks), 256, 0, s>>>(words, nw, r_bits,
+                                                                                out);
+    BM_CUDA_TRY(cudaGetLastError());
+    return BM_OK;
+}
+
+}  // namespace bm

@@ -1,0 +1,131 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <vector>
+
+#include "../../include/bm.h"
+
+#define BM_CUDA_TRY(expr)                                  \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) {                           \
+            bm_note_cuda_error(e_, #expr, __FILE__, __LINE__); \
+            return BM_ECUDA;                               \
+        }                                                  \
+    } while (0)
+
+void bm_note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+namespace bm {
+
+// Rows covered by one entry of a position list's tile index.
+constexpr uint32_t kListTileRows = 8192;
+// Most threshold transitions a predicate evaluates as comparators before it
+// switches to a per-row table lookup.
+constexpr int kMaxTransitions = 8;
+// Bounded device waits give up after this many nanoseconds of %globaltimer.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+// Device error word bits.
+constexpr int kErrTimeout = 1;
+
+// A symmetric predicate f over counts 0..n, compiled on the host
+// (Sec. 4.3: intervals and general symmetric functions from thresholds).
+//   mode 0: constant v0.
+//   mode 1: f(c) = v0 XOR [c >= t_1] XOR ... XOR [c >= t_m]  (t strictly
+//           increasing, 1 <= t <= n).  Because the threshold sets are nested,
+//           an interval [L, U] is T_L AND NOT T_{U+1}.
+//   mode 2: per-row lookup of bit c of `table` (m > kMaxTransitions).
+struct Pred {
+    uint32_t mode;
+    uint32_t v0;
+    uint32_t ntrans;
+    uint32_t table_words32;  // mode 2: 32-bit words of the table
+    uint32_t trans[kMaxTransitions];
+    const uint32_t* table;   // mode 2: device, bit c of word c/32
+};
+
+// Compile a truth table f(0..n) (host bytes 0/1) into a predicate.  The
+// caller places the table on the device for mode 2.
+Pred compile_pred(const uint8_t* f, uint32_t n);
+// f for the threshold theta / the interval [lo, hi], as bytes f(0..n).
+void threshold_truth(uint32_t n, uint32_t theta, std::vector<uint8_t>& f);
+void interval_truth(uint32_t n, uint32_t lo, uint32_t hi, std::vector<uint8_t>& f);
+
+// Arguments of one dense query launch.
+struct DenseArgs {
+    const uint64_t* base;     // pool dense storage
+    uint64_t stride_words;    // words between bitmaps (multiple of 32)
+    uint64_t words;           // ceil(r / 64)
+    uint64_t r_bits;
+    const uint32_t* ids;      // device, n ids
+    uint32_t n;
+    Pred pred;
+    uint64_t* out;            // device, `words` words
+    unsigned long long* card; // device, pre-zeroed accumulator (may be null)
+    int* err;                 // device error word
+};
+
+// Dense kernel variants (the autotuner picks one per shape).
+struct DenseConfig {
+    int variant;   // 0 = direct 128-bit loads, 1 = bulk-copy (TMA) pipeline in shared memory
+    int threads;   // consumer threads per CTA
+    int stages;    // pipeline depth (variant 1)
+    int ctas_per_sm;
+};
+
+int launch_dense(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStream_t s);
+int launch_cardinality(const uint64_t* words, uint64_t r_bits, unsigned long long* out,
+                       int sm_count, cudaStream_t s);
+int planes_for(uint32_t n);  // counter planes needed for counts 0..n
+
+}  // namespace bm
+
+// Per-call host->device staging: pinned host block + device block + event.
+struct bm_stage_slot {
+    void* h = nullptr;
+    void* d = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool used = false;
+};
+
+struct bm_pool {
+    int device = 0;
+    int sm_count = 0;
+    uint64_t r_bits = 0, words = 0, stride_words = 0;
+    uint32_t capacity = 0;
+    uint64_t mem_budget = 0, device_bytes = 0;
+
+    uint64_t* d_dense = nullptr;          // capacity * stride_words
+    std::vector<uint8_t> dense_present;
+    std::vector<uint64_t> card;           // per id cardinality, host copy
+
+    // position lists: one growable device arena
+    uint32_t* d_pos = nullptr;
+    uint64_t pos_cap = 0, pos_used = 0;
+    std::vector<uint64_t> list_begin, list_len;  // host, per id
+    std::vector<uint8_t> list_present;
+    uint32_t* d_tile_index = nullptr;     // capacity * tiles_per_list (+1)
+    uint64_t* d_list_begin = nullptr;     // per id, device copy
+    uint32_t tiles_per_list = 0;
+
+    int* d_err = nullptr;
+    static constexpr int kSlots = 8;
+    bm_stage_slot slots[kSlots];
+    int next_slot = 0;
+    bm::DenseConfig dense_cfg{0, 256, 4, 2};
+    std::mutex mu;
+};
+
+namespace bm {
+// Reserve a staging slot of at least `bytes`, waiting for its previous use.
+int stage_acquire(bm_pool* p, size_t bytes, bm_stage_slot** out);
+// Copy the slot's first `bytes` to the device on `s` and mark its reuse point.
+int stage_commit(bm_stage_slot* slot, size_t bytes, cudaStream_t s);
+int stage_release(bm_stage_slot* slot, cudaStream_t s);
+int track_alloc(bm_pool* p, void** ptr, size_t bytes);
+}  // namespace bm
