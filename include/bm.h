@@ -176,6 +176,44 @@ int bm_symmetric(bm_pool* pool, const uint32_t* ids, uint32_t n, const uint64_t*
  */
 int bm_cardinality(const uint64_t* words, uint64_t r_bits, uint64_t* out_card, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Threshold query that allocates nothing (no counterpart in the paper)
+ * ---------------------------------------------------------------------- */
+
+/* Largest n accepted by bm_threshold_noalloc (size of its fixed scratch). */
+#define BM_NOALLOC_MAX_N 16384u
+
+/*
+ * For callers that cannot call cudaMalloc: for example a plugin inside a host
+ * program that owns every device allocation, or a service that must not
+ * allocate (and so must not risk an allocation's implicit synchronisation or
+ * failure) once it is running.  The paper has no counterpart: it is an
+ * interface choice of this library.
+ *
+ * Same result as bm_threshold, computed by the same dense kernel, but on the
+ * caller's own bitmaps and with no pool: bitmap j (0 <= j < n_bitmaps) is
+ * words + j * stride_words, ceil(r_bits / 64) words.  `words` must be
+ * 16-byte aligned, stride_words even and >= ceil(r_bits / 64) rounded up to
+ * even, and every bitmap readable up to that rounded length.  ids is a host
+ * array of n ids; out_words (device, ceil(r_bits / 64) words) and out_card
+ * (device uint64, may be NULL) are written as by bm_threshold.
+ *
+ * Scratch: the ids are copied into one fixed device array of
+ * BM_NOALLOC_MAX_N uint32 declared in the library; every GPU that loads the
+ * library holds it until the process exits.  n > BM_NOALLOC_MAX_N is
+ * rejected with BM_EINVAL.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call shares the array and it
+ * keeps the previous call's ids, so calls whose work overlaps on the GPU
+ * (different streams, no ordering between them) race on it: order them.
+ * No cudaMalloc, cudaFree or other allocating routine is called.
+ * Errors: BM_EINVAL (NULL pointer, n = 0 or too large, bad alignment or
+ * stride, r_bits = 0 or > 2^32), BM_ERANGE (an id >= n_bitmaps), BM_ECUDA.
+ */
+int bm_threshold_noalloc(const uint64_t* words, uint64_t stride_words, uint32_t n_bitmaps,
+                         uint64_t r_bits, const uint32_t* ids, uint32_t n, uint32_t theta,
+                         uint64_t* out_words, uint64_t* out_card, void* stream);
+
 /* Static text for a status code. */
 const char* bm_strerror(int code);
 

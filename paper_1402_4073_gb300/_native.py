@@ -37,6 +37,7 @@ SIGNATURES = {
     "bm_threshold": (i32, [vp, vp, u32, u32, vp, vp, vp]),
     "bm_symmetric": (i32, [vp, vp, u32, vp, vp, vp, vp]),
     "bm_cardinality": (i32, [vp, u64, vp, vp]),
+    "bm_threshold_noalloc": (i32, [vp, u64, u32, u64, vp, u32, u32, vp, vp, vp]),
 }
 
 
