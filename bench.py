@@ -203,8 +203,16 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0,
                     help="seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--r-log2", type=int, default=26,
+                    help="rows = 2^r_log2 (smaller cases are for profiling only)")
+    ap.add_argument("--dense-config", default="",
+                    help="variant,threads,stages,ctas_per_sm: skip the variant search")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    global R_BITS, WORKLOAD
+    if args.r_log2 != 26:
+        R_BITS = 1 << args.r_log2
+        WORKLOAD = WORKLOAD.replace("r=2^26", f"r=2^{args.r_log2}")
     if args.impl == "reference":
         return run_reference(args)
 
@@ -237,6 +245,8 @@ def main():
     # pick the dense feeding variant by timing a few candidates (results are identical)
     candidates = [(1, 128, 4, 1), (1, 128, 3, 1), (1, 64, 6, 2), (1, 64, 4, 3), (0, 256, 4, 2),
                   (0, 256, 4, 3)]
+    if args.dense_config:
+        candidates = [tuple(int(x) for x in args.dense_config.split(","))]
     best, best_t = None, 1e30
     for c in candidates:
         pool.set_dense_config(*c)
@@ -251,6 +261,7 @@ def main():
         t = e0.elapsed_time(e1)
         if t < best_t:
             best, best_t = c, t
+        print(f"dense config {c}: {t / 5 * 1e3:.1f} us per query", file=sys.stderr)
     pool.set_dense_config(*best)
     pool.status()
 
