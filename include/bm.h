@@ -138,10 +138,21 @@ int bm_pool_status(bm_pool* pool);
  *              `threads` consumer threads per CTA (64 or 128) and `stages`
  *              pipeline stages (2..8) of 16 bitmaps each.
  * ctas_per_sm (1..8) caps the persistent grid at ctas_per_sm x SM count.
+ * adder: layout of the adder tree (Sec. 4.3 "Sideways Sum"): 0 = blocks of
+ * 16 inputs through 15 full adders, 1 = blocks of 8 inputs through 7 (fewer
+ * live registers, one more carry ripple per 8 inputs); variant 0 only.
  * BM_EINVAL for values outside these ranges.
  */
 int bm_pool_set_dense_config(bm_pool* pool, int variant, int threads, int stages,
-                             int ctas_per_sm);
+                             int ctas_per_sm, int adder);
+
+/*
+ * Choose the sparse (ScanCount) kernel's shape: tile_rows rows of counters
+ * per CTA (a multiple of 8192, at most 65536 with 16-bit counters),
+ * `threads` per CTA (64..512, a multiple of 32), ctas_per_sm (1..8).
+ * BM_EINVAL outside these ranges.
+ */
+int bm_pool_set_sparse_config(bm_pool* pool, uint32_t tile_rows, int threads, int ctas_per_sm);
 
 /* ------------------------------------------------------------------------
  * Single queries
@@ -169,12 +180,130 @@ int bm_threshold(bm_pool* pool, const uint32_t* ids, uint32_t n, uint32_t theta,
 int bm_symmetric(bm_pool* pool, const uint32_t* ids, uint32_t n, const uint64_t* table,
                  uint64_t* out_words, uint64_t* out_card, void* stream);
 
+/* Query kinds of bm_query. */
+#define BM_KIND_THRESHOLD 0u /* count >= theta */
+#define BM_KIND_INTERVAL 1u  /* lo <= count <= hi (T_lo AND NOT T_{hi+1}, Sec. 4.3) */
+#define BM_KIND_TABLE 2u     /* f(count) from a truth table */
+
+/* Kernel paths of bm_query.  Results are identical on every path. */
+#define BM_PATH_AUTO 0   /* the pool's selector chooses (learned model, else a density rule) */
+#define BM_PATH_DENSE 1  /* bit-sliced carry-save counter over the dense words */
+#define BM_PATH_SPARSE 2 /* ScanCount over the position lists (every id needs a list) */
+
+typedef struct bm_query {
+    const uint32_t* ids;    /* host array of n pool ids (repeats allowed) */
+    uint32_t n;             /* 1 .. BM_N_MAX */
+    uint32_t kind;          /* BM_KIND_* */
+    uint32_t theta;         /* BM_KIND_THRESHOLD */
+    uint32_t lo, hi;        /* BM_KIND_INTERVAL (hi is clamped to n) */
+    const uint64_t* table;  /* BM_KIND_TABLE: host, ceil((n+1)/64) words, bit c = f(c) */
+    uint64_t* out_words;    /* device, ceil(r/64) words, written in full */
+    int32_t path;           /* BM_PATH_* */
+    uint32_t reserved;      /* must be 0 */
+} bm_query;
+
+/*
+ * Run one query on the path it names.  out_card: device uint64 or NULL.
+ * *chosen_path (may be NULL) receives the path that ran.  Errors as
+ * bm_threshold, plus BM_EINVAL for a bad kind/path and BM_ERANGE when the
+ * sparse path is asked for an id without a position list.
+ */
+int bm_query_run(bm_pool* pool, const bm_query* q, uint64_t* out_card, int32_t* chosen_path,
+                 void* stream);
+
+/*
+ * Batched queries (not in the paper, which runs one query at a time): run
+ * the nq queries q[0..nq) as one replay of a CUDA graph holding two
+ * persistent kernels.  Dense queries are cut into (32768-row slab, query)
+ * items taken slab-major, so each slab of the pool is read from HBM once
+ * and served from L2 to every query of the batch that reads it; sparse
+ * queries into (query, row tile) ScanCount items.  BM_PATH_AUTO queries are
+ * routed by the learned selector when one is installed (its network runs on
+ * the device for the whole batch), else by the density rule.
+ * out_cards: device, nq uint64, receives each query's cardinality.
+ * chosen_paths: host, nq entries (may be NULL), receives each query's path.
+ * Every result equals that of the same query run alone.  Host arrays are
+ * copied before the call returns; up to three batches may be in flight.
+ * Errors as bm_query_run, for the first failing query (nothing is launched).
+ */
+int bm_threshold_batch(bm_pool* pool, const bm_query* q, uint32_t nq, uint64_t* out_cards,
+                       int32_t* chosen_paths, void* stream);
+
+/*
+ * Batch kernel shape: dense persistent CTAs per SM (1 or 2) and adder layout
+ * (as in bm_pool_set_dense_config).  Results are identical for every choice.
+ */
+int bm_pool_set_batch_config(bm_pool* pool, int ctas_per_sm, int adder);
+
 /*
  * Number of ones among the first r_bits rows of a device bitmap `words`
  * (ceil(r/64) words), written to the device uint64 *out_card (Sec. 2.1: the
  * cardinality of the set a bitmap stores).  Asynchronous on `stream`.
  */
 int bm_cardinality(const uint64_t* words, uint64_t r_bits, uint64_t* out_card, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned kernel selector (not in the paper: the paper compares its
+ * algorithms by measured time per query and reports each one's
+ * "suboptimality", the extra time over the best, App. C; here a small
+ * network predicts that time so the fastest kernel can be picked)
+ * ---------------------------------------------------------------------- */
+
+/* Number of selector features and candidates (the network's in/outputs). */
+#define BM_SELECTOR_FEATURES 5u
+#define BM_SELECTOR_HIDDEN 64u
+#define BM_SELECTOR_CANDIDATES 4u
+/*
+ * Candidate c runs: 0 = dense counter; 1, 2, 3 = ScanCount with tiles of
+ * 16384, 32768, 65536 rows.
+ */
+
+/*
+ * Features of a query (5 floats, host): log2 n; the first count where f
+ * changes, divided by n (theta / n for a threshold); log10 of the mean and of
+ * the largest input density (cardinality / r, floored at 1e-9); log2 r.
+ */
+int bm_query_features(const bm_pool* pool, const bm_query* q, float* out);
+
+/*
+ * Install a trained selector: params (host fp32, the layout of
+ * bm_mlp_forward with F = 5, H = 64, C = 4) predicts each candidate's log
+ * time from the standardised features (x - mean) / std.  Queries with
+ * path BM_PATH_AUTO then run the candidate with the smallest prediction
+ * among those whose inputs are loaded.  params = NULL removes it (the fixed
+ * density rule applies).  Results never depend on the choice.
+ */
+int bm_pool_set_selector(bm_pool* pool, const float* params, uint64_t nparams, const float* mean,
+                         const float* stdev, uint32_t n_out);
+
+/* The path and sparse tile rows that BM_PATH_AUTO would pick for q. */
+int bm_query_select(const bm_pool* pool, const bm_query* q, int32_t* path, uint32_t* tile_rows);
+
+/*
+ * Network F -> H -> H -> C with ReLU after the two hidden layers, fp32,
+ * device buffers.  params: W1[F][H], b1[H], W2[H][H], b2[H], W3[H][C], b3[C]
+ * (weights [in][out], row-major).  x: [batch][F]; h1, h2: [batch][H]
+ * (written, kept for the backward pass); y: [batch][C].
+ */
+int bm_mlp_forward(const float* params, uint32_t F, uint32_t H, uint32_t C, const float* x,
+                   uint32_t batch, float* h1, float* h2, float* y, void* stream);
+
+/*
+ * Gradients of L = sum((y - target)^2) / (batch * C) with respect to every
+ * parameter, written to `grads` (the layout of params), from the forward
+ * pass's x, h1, h2, y.  workspace: device, batch * (C + 2H) floats.
+ * loss: device float receiving L, or NULL.
+ */
+int bm_mlp_backward(const float* params, uint32_t F, uint32_t H, uint32_t C, const float* x,
+                    const float* h1, const float* h2, const float* y, const float* target,
+                    uint32_t batch, float* grads, float* workspace, float* loss, void* stream);
+
+/*
+ * One Adam step (Kingma and Ba 2015, bias-corrected; step is 1-based) over
+ * `count` parameters, updating params, m and v in place on the device.
+ */
+int bm_mlp_adam(float* params, const float* grads, float* m, float* v, uint64_t count,
+                uint32_t step, float lr, float beta1, float beta2, float eps, void* stream);
 
 /* ------------------------------------------------------------------------
  * Threshold query that allocates nothing (no counterpart in the paper)

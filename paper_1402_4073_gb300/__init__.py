@@ -142,9 +142,18 @@ class Pool:
         check(lib.bm_pool_status(self.handle), "bm_pool_status")
 
     def set_dense_config(self, variant: int, threads: int = 128, stages: int = 4,
-                         ctas_per_sm: int = 1) -> None:
-        check(lib.bm_pool_set_dense_config(self.handle, variant, threads, stages, ctas_per_sm),
-              "bm_pool_set_dense_config")
+                         ctas_per_sm: int = 1, adder: int = 0) -> None:
+        check(lib.bm_pool_set_dense_config(self.handle, variant, threads, stages, ctas_per_sm,
+                                           adder), "bm_pool_set_dense_config")
+
+    def set_sparse_config(self, tile_rows: int = 32768, threads: int = 512,
+                          ctas_per_sm: int = 2) -> None:
+        check(lib.bm_pool_set_sparse_config(self.handle, tile_rows, threads, ctas_per_sm),
+              "bm_pool_set_sparse_config")
+
+    def set_batch_config(self, ctas_per_sm: int = 2, adder: int = 0) -> None:
+        check(lib.bm_pool_set_batch_config(self.handle, ctas_per_sm, adder),
+              "bm_pool_set_batch_config")
 
     def empty_words(self, n: int | None = None) -> torch.Tensor:
         shape = (self.words,) if n is None else (n, self.words)
@@ -187,3 +196,131 @@ def interval_table(n: int, lo: int, hi: int) -> np.ndarray:
 
 def to_numpy_words(t: torch.Tensor) -> np.ndarray:
     return t.detach().cpu().numpy().view(np.uint64)
+
+
+# ---------------------------------------------------------------------------
+# query descriptors, path choice, batches
+
+KIND_THRESHOLD, KIND_INTERVAL, KIND_TABLE = 0, 1, 2
+PATH_AUTO, PATH_DENSE, PATH_SPARSE = 0, 1, 2
+SELECTOR_FEATURES, SELECTOR_HIDDEN, SELECTOR_CANDIDATES = 5, 64, 4
+# candidate c of the selector: (path, sparse tile rows)
+CANDIDATES = [(PATH_DENSE, 0), (PATH_SPARSE, 16384), (PATH_SPARSE, 32768), (PATH_SPARSE, 65536)]
+
+
+def make_query(ids, kind: int = KIND_THRESHOLD, theta: int = 0, lo: int = 0, hi: int = 0,
+               table=None, out_words: torch.Tensor | None = None, path: int = PATH_AUTO):
+    """A bm_query struct plus the host arrays it points into (keep both alive)."""
+    i = _host_u32(ids)
+    t = _host_u64(table) if table is not None else None
+    q = _native.bm_query()
+    q.ids = i.ctypes.data if len(i) else None
+    q.n = len(i)
+    q.kind = kind
+    q.theta, q.lo, q.hi = int(theta), int(lo), int(hi)
+    q.table = t.ctypes.data if t is not None else None
+    q.out_words = _dev_ptr(out_words) if out_words is not None else None
+    q.path = path
+    q.reserved = 0
+    return q, (i, t)
+
+
+def _q_from(obj, out_words=None, path=None):
+    return make_query(obj.ids, obj.kind, getattr(obj, "theta", 0), getattr(obj, "lo", 0),
+                      getattr(obj, "hi", 0), getattr(obj, "table", None), out_words,
+                      PATH_AUTO if path is None else path)
+
+
+def query_run(pool: Pool, query, out_words: torch.Tensor, out_card: torch.Tensor | None = None,
+              path: int = PATH_AUTO, stream=None) -> int:
+    """Run one query (an object with ids, kind, theta, lo, hi, table) on a path;
+    returns the path that ran."""
+    if out_words.numel() * out_words.element_size() < 8 * pool.words:
+        raise ValueError("output buffer too small")
+    q, keep = _q_from(query, out_words, path)
+    chosen = ctypes.c_int32()
+    check(lib.bm_query_run(pool.handle, ctypes.byref(q), _dev_ptr(out_card, 8),
+                           ctypes.byref(chosen), _stream(stream)), "bm_query_run")
+    return int(chosen.value)
+
+
+def threshold_batch(pool: Pool, queries, outs, out_cards: torch.Tensor, paths=None,
+                    stream=None) -> np.ndarray:
+    """Run a batch of queries (objects with ids, kind, theta, lo, hi, table)
+    into outs[i]; cardinalities into out_cards[i].  Returns the chosen paths."""
+    nq = len(queries)
+    if out_cards.numel() < nq:
+        raise ValueError("out_cards too small")
+    arr = (_native.bm_query * nq)()
+    keep = []
+    for i, qo in enumerate(queries):
+        if outs[i].numel() * outs[i].element_size() < 8 * pool.words:
+            raise ValueError("output buffer too small")
+        q, k = _q_from(qo, outs[i], None if paths is None else int(paths[i]))
+        arr[i] = q
+        keep.append(k)
+    chosen = np.zeros(nq, dtype=np.int32)
+    check(lib.bm_threshold_batch(pool.handle, arr, nq, _dev_ptr(out_cards, 8 * nq),
+                                 chosen.ctypes.data, _stream(stream)), "bm_threshold_batch")
+    return chosen
+
+
+def query_features(pool: Pool, query) -> np.ndarray:
+    q, keep = _q_from(query)
+    out = np.zeros(SELECTOR_FEATURES, dtype=np.float32)
+    check(lib.bm_query_features(pool.handle, ctypes.byref(q), out.ctypes.data), "bm_query_features")
+    return out
+
+
+def query_select(pool: Pool, query) -> tuple[int, int]:
+    q, keep = _q_from(query)
+    path, tile = ctypes.c_int32(), ctypes.c_uint32()
+    check(lib.bm_query_select(pool.handle, ctypes.byref(q), ctypes.byref(path), ctypes.byref(tile)),
+          "bm_query_select")
+    return int(path.value), int(tile.value)
+
+
+def set_selector(pool: Pool, params: np.ndarray | None, mean=None, std=None) -> None:
+    if params is None:
+        check(lib.bm_pool_set_selector(pool.handle, None, 0, None, None, 0), "bm_pool_set_selector")
+        return
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    m = np.ascontiguousarray(mean, dtype=np.float32)
+    s = np.ascontiguousarray(std, dtype=np.float32)
+    check(lib.bm_pool_set_selector(pool.handle, p.ctypes.data, p.size, m.ctypes.data, s.ctypes.data,
+                                   SELECTOR_CANDIDATES), "bm_pool_set_selector")
+
+
+# ---------------------------------------------------------------------------
+# selector network kernels (fp32, device tensors)
+
+def mlp_param_count(F: int = 5, H: int = 64, C: int = 4) -> int:
+    return F * H + H + H * H + H + H * C + C
+
+
+def mlp_forward(params: torch.Tensor, x: torch.Tensor, H: int, C: int, stream=None):
+    B, F = x.shape
+    h1 = torch.empty(B, H, dtype=torch.float32, device=x.device)
+    h2 = torch.empty(B, H, dtype=torch.float32, device=x.device)
+    y = torch.empty(B, C, dtype=torch.float32, device=x.device)
+    check(lib.bm_mlp_forward(_dev_ptr(params), F, H, C, _dev_ptr(x), B, _dev_ptr(h1), _dev_ptr(h2),
+                             _dev_ptr(y), _stream(stream)), "bm_mlp_forward")
+    return y, h1, h2
+
+
+def mlp_backward(params: torch.Tensor, x, h1, h2, y, target, stream=None):
+    B, F = x.shape
+    H, C = h1.shape[1], y.shape[1]
+    grads = torch.empty_like(params)
+    ws = torch.empty(B * (C + 2 * H), dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    check(lib.bm_mlp_backward(_dev_ptr(params), F, H, C, _dev_ptr(x), _dev_ptr(h1), _dev_ptr(h2),
+                              _dev_ptr(y), _dev_ptr(target), B, _dev_ptr(grads), _dev_ptr(ws),
+                              _dev_ptr(loss), _stream(stream)), "bm_mlp_backward")
+    return grads, loss
+
+
+def mlp_adam(params, grads, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+             eps: float = 1e-8, stream=None) -> None:
+    check(lib.bm_mlp_adam(_dev_ptr(params), _dev_ptr(grads), _dev_ptr(m), _dev_ptr(v), params.numel(),
+                          step, lr, beta1, beta2, eps, _stream(stream)), "bm_mlp_adam")

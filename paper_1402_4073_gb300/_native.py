@@ -17,6 +17,11 @@ u64, u32, i32, vp, dbl = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.
 P64 = ctypes.POINTER(ctypes.c_uint64)
 
 
+class bm_query(ctypes.Structure):
+    _fields_ = [("ids", vp), ("n", u32), ("kind", u32), ("theta", u32), ("lo", u32), ("hi", u32),
+                ("table", vp), ("out_words", vp), ("path", ctypes.c_int32), ("reserved", u32)]
+
+
 class bm_pool_info_t(ctypes.Structure):
     _fields_ = [("r_bits", u64), ("words", u64), ("stride_words", u64), ("capacity", u32),
                 ("dense_loaded", u32), ("lists_loaded", u32), ("sm_count", u32),
@@ -33,10 +38,21 @@ SIGNATURES = {
     "bm_pool_info": (i32, [vp, ctypes.POINTER(bm_pool_info_t)]),
     "bm_pool_bitmap_cardinality": (i32, [vp, u32, P64]),
     "bm_pool_status": (i32, [vp]),
-    "bm_pool_set_dense_config": (i32, [vp, i32, i32, i32, i32]),
+    "bm_pool_set_dense_config": (i32, [vp, i32, i32, i32, i32, i32]),
+    "bm_threshold_batch": (i32, [vp, vp, u32, vp, vp, vp]),
+    "bm_pool_set_batch_config": (i32, [vp, i32, i32]),
     "bm_threshold": (i32, [vp, vp, u32, u32, vp, vp, vp]),
     "bm_symmetric": (i32, [vp, vp, u32, vp, vp, vp, vp]),
     "bm_cardinality": (i32, [vp, u64, vp, vp]),
+    "bm_pool_set_sparse_config": (i32, [vp, u32, i32, i32]),
+    "bm_query_run": (i32, [vp, vp, vp, vp, vp]),
+    "bm_query_features": (i32, [vp, vp, vp]),
+    "bm_pool_set_selector": (i32, [vp, vp, u64, vp, vp, u32]),
+    "bm_query_select": (i32, [vp, vp, vp, vp]),
+    "bm_mlp_forward": (i32, [vp, u32, u32, u32, vp, u32, vp, vp, vp, vp]),
+    "bm_mlp_backward": (i32, [vp, u32, u32, u32, vp, vp, vp, vp, vp, u32, vp, vp, vp, vp]),
+    "bm_mlp_adam": (i32, [vp, vp, vp, vp, u64, u32, ctypes.c_float, ctypes.c_float,
+                          ctypes.c_float, ctypes.c_float, vp]),
     "bm_threshold_noalloc": (i32, [vp, u64, u32, u64, vp, u32, u32, vp, vp, vp]),
 }
 

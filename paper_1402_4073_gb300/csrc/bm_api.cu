@@ -1,9 +1,10 @@
 // Single-query entry points: host validation, predicate compilation,
-// staging of ids and truth tables, dense kernel launch.
+// staging of ids and truth tables, path choice and kernel launch.
 #include <algorithm>
 #include <cstring>
 
 #include "bm_device.cuh"
+#include "bm_select.h"
 
 namespace bm {
 
@@ -38,22 +39,36 @@ Pred compile_pred(const uint8_t* f, uint32_t n) {
     return p;
 }
 
-}  // namespace bm
+int query_truth(const bm_query* q, std::vector<uint8_t>& f) {
+    switch (q->kind) {
+        case BM_KIND_THRESHOLD: threshold_truth(q->n, q->theta, f); return BM_OK;
+        case BM_KIND_INTERVAL: interval_truth(q->n, q->lo, q->hi, f); return BM_OK;
+        case BM_KIND_TABLE:
+            if (!q->table) return BM_EINVAL;
+            f.assign((size_t)q->n + 1, 0);
+            for (uint32_t c = 0; c <= q->n; ++c)
+                f[c] = (uint8_t)((q->table[c >> 6] >> (c & 63)) & 1u);
+            return BM_OK;
+        default: return BM_EINVAL;
+    }
+}
 
-using namespace bm;
-
-namespace {
-
-int validate_ids(const bm_pool* p, const uint32_t* ids, uint32_t n) {
+int validate_ids(const bm_pool* p, const uint32_t* ids, uint32_t n, int path) {
     if (!ids || n == 0 || n > BM_N_MAX) return BM_EINVAL;
-    for (uint32_t k = 0; k < n; ++k)
-        if (ids[k] >= p->capacity || !p->dense_present[ids[k]]) return BM_ERANGE;
+    for (uint32_t k = 0; k < n; ++k) {
+        if (ids[k] >= p->capacity) return BM_ERANGE;
+        if (path == BM_PATH_DENSE && !p->dense_present[ids[k]]) return BM_ERANGE;
+        if (path == BM_PATH_SPARSE && !p->list_present[ids[k]]) return BM_ERANGE;
+        if (path == BM_PATH_AUTO && !p->dense_present[ids[k]] && !p->list_present[ids[k]])
+            return BM_ERANGE;
+    }
     return BM_OK;
 }
 
-// Stage ids (and a mode-2 table) and launch the dense kernel.
-int run_dense(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<uint8_t>& f,
-              uint64_t* out_words, uint64_t* out_card, cudaStream_t s) {
+// Stage ids (and a table-mode truth table) and launch the chosen kernel.
+int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<uint8_t>& f,
+               int path, uint32_t tile_rows, uint64_t* out_words, uint64_t* out_card,
+               cudaStream_t s) {
     Pred pred = compile_pred(f.data(), n);
     const size_t ids_bytes = ((size_t)n * 4 + 15) & ~(size_t)15;
     const size_t tab_bytes = pred.mode == 2 ? (size_t)pred.table_words32 * 4 : 0;
@@ -71,23 +86,42 @@ int run_dense(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<uin
     rc = stage_commit(sl, ids_bytes + tab_bytes, s);
     if (rc) return rc;
     if (out_card) BM_CUDA_TRY(cudaMemsetAsync(out_card, 0, 8, s));
-    DenseArgs a{};
-    a.base = p->d_dense;
-    a.stride_words = p->stride_words;
-    a.words = p->words;
-    a.r_bits = p->r_bits;
-    a.ids = static_cast<const uint32_t*>(sl->d);
-    a.n = n;
-    a.pred = pred;
-    a.out = out_words;
-    a.card = reinterpret_cast<unsigned long long*>(out_card);
-    a.err = p->d_err;
-    rc = launch_dense(a, p->dense_cfg, p->sm_count, s);
+    const uint32_t* d_ids = static_cast<const uint32_t*>(sl->d);
+    if (path == BM_PATH_SPARSE) {
+        SparseArgs a{};
+        a.positions = p->d_pos;
+        a.list_begin = p->d_list_begin;
+        a.tile_index = p->d_tile_index;
+        a.tiles_per_list = p->tiles_per_list;
+        a.tile_rows = tile_rows ? tile_rows : p->sparse_cfg.tile_rows;
+        a.r_bits = p->r_bits;
+        a.ids = d_ids;
+        a.n = n;
+        a.pred = pred;
+        a.out = out_words;
+        a.card = reinterpret_cast<unsigned long long*>(out_card);
+        rc = launch_sparse(a, p->sparse_cfg, p->sm_count, s);
+    } else {
+        DenseArgs a{};
+        a.base = p->d_dense;
+        a.stride_words = p->stride_words;
+        a.words = p->words;
+        a.r_bits = p->r_bits;
+        a.ids = d_ids;
+        a.n = n;
+        a.pred = pred;
+        a.out = out_words;
+        a.card = reinterpret_cast<unsigned long long*>(out_card);
+        a.err = p->d_err;
+        rc = launch_dense(a, p->dense_cfg, p->sm_count, s);
+    }
     int rc2 = stage_release(sl, s);
     return rc ? rc : rc2;
 }
 
-}  // namespace
+}  // namespace bm
+
+using namespace bm;
 
 extern "C" {
 
@@ -95,24 +129,53 @@ int bm_threshold(bm_pool* p, const uint32_t* ids, uint32_t n, uint32_t theta,
                  uint64_t* out_words, uint64_t* out_card, void* stream) {
     if (!p || !out_words) return BM_EINVAL;
     std::lock_guard<std::mutex> lk(p->mu);
-    int rc = validate_ids(p, ids, n);
+    int rc = validate_ids(p, ids, n, BM_PATH_DENSE);
     if (rc) return rc;
     BM_CUDA_TRY(cudaSetDevice(p->device));
     std::vector<uint8_t> f;
     threshold_truth(n, theta, f);
-    return run_dense(p, ids, n, f, out_words, out_card, static_cast<cudaStream_t>(stream));
+    return run_single(p, ids, n, f, BM_PATH_DENSE, 0, out_words, out_card,
+                      static_cast<cudaStream_t>(stream));
 }
 
 int bm_symmetric(bm_pool* p, const uint32_t* ids, uint32_t n, const uint64_t* table,
                  uint64_t* out_words, uint64_t* out_card, void* stream) {
     if (!p || !out_words || !table) return BM_EINVAL;
     std::lock_guard<std::mutex> lk(p->mu);
-    int rc = validate_ids(p, ids, n);
+    int rc = validate_ids(p, ids, n, BM_PATH_DENSE);
     if (rc) return rc;
     BM_CUDA_TRY(cudaSetDevice(p->device));
     std::vector<uint8_t> f((size_t)n + 1);
     for (uint32_t c = 0; c <= n; ++c) f[c] = (uint8_t)((table[c >> 6] >> (c & 63)) & 1u);
-    return run_dense(p, ids, n, f, out_words, out_card, static_cast<cudaStream_t>(stream));
+    return run_single(p, ids, n, f, BM_PATH_DENSE, 0, out_words, out_card,
+                      static_cast<cudaStream_t>(stream));
+}
+
+int bm_query_run(bm_pool* p, const bm_query* q, uint64_t* out_card, int32_t* chosen_path,
+                 void* stream) {
+    if (!p || !q || !q->out_words || q->reserved) return BM_EINVAL;
+    if (q->path < BM_PATH_AUTO || q->path > BM_PATH_SPARSE) return BM_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    int rc = validate_ids(p, q->ids, q->n, q->path);
+    if (rc) return rc;
+    std::vector<uint8_t> f;
+    rc = query_truth(q, f);
+    if (rc) return rc;
+    BM_CUDA_TRY(cudaSetDevice(p->device));
+    Candidate c{q->path, 0};
+    if (q->path == BM_PATH_AUTO) c = select_candidate(p, q->ids, q->n, f);
+    if (chosen_path) *chosen_path = c.path;
+    return run_single(p, q->ids, q->n, f, c.path, c.tile_rows, q->out_words, out_card,
+                      static_cast<cudaStream_t>(stream));
+}
+
+int bm_pool_set_sparse_config(bm_pool* p, uint32_t tile_rows, int threads, int ctas_per_sm) {
+    if (!p || tile_rows == 0 || tile_rows % kListTileRows || tile_rows > 65536) return BM_EINVAL;
+    if (threads < 64 || threads > 512 || threads % 32 || ctas_per_sm < 1 || ctas_per_sm > 8)
+        return BM_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->sparse_cfg = SparseConfig{tile_rows, threads, ctas_per_sm};
+    return BM_OK;
 }
 
 }  // extern "C"

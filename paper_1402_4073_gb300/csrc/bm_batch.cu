@@ -1,0 +1,545 @@
+// Batched queries: many queries of uneven n, predicate and path in one
+// CUDA-graph launch of two persistent kernels.
+//
+//  * Dense items are (column tile, query) pairs taken tile-major from an
+//    atomic work counter, so at any moment the CTAs of the GPU work on the
+//    same 32768-row slab of the pool: each input slab is read from HBM once
+//    and then served from L2 to every other query that reads it.
+//  * Sparse items are (query, row tile) pairs of the ScanCount kernel with
+//    16-bit shared-memory counters and each query's own tile size.
+//  * A zeroing kernel resets the work counters and the caller's
+//    cardinalities.  All three read their arguments from a device-side
+//    descriptor block, so the captured graph is replayed unchanged for every
+//    batch; only the block is copied to the device before each replay.
+#include <algorithm>
+#include <cstring>
+#include <map>
+
+#include "bm_dense_common.cuh"
+#include "bm_select.h"
+
+namespace bm {
+
+constexpr int kBatchThreads = 256;        // dense: one 16-byte column per thread
+constexpr int kSparseBatchThreads = 512;
+constexpr uint32_t kSparseMaxTile = 65536;
+
+struct QueryDesc {
+    const uint32_t* ids;
+    uint32_t n;
+    uint32_t tile_rows;
+    uint64_t* out;
+    Pred pred;
+};
+
+struct BatchHeader {
+    uint64_t* out_cards;
+    const QueryDesc* desc;
+    const uint32_t* dense_list;
+    const uint32_t* sparse_list;
+    const uint64_t* sparse_off;  // n_sparse + 1 prefix sums of sparse items
+    uint32_t nq, n_dense, n_sparse, pad;
+    uint64_t dense_items;
+    unsigned long long dense_next, sparse_next;
+};
+
+struct BatchPoolArgs {
+    const uint64_t* base;
+    uint64_t stride_words, words, r_bits;
+    const uint32_t* positions;
+    const uint64_t* list_begin;
+    const uint32_t* tile_index;
+    uint32_t tiles_per_list;
+};
+
+namespace {
+
+using namespace dev;
+
+__global__ void batch_zero_kernel(BatchHeader* h) {
+    for (uint32_t i = threadIdx.x; i < h->nq; i += blockDim.x) h->out_cards[i] = 0;
+    if (threadIdx.x == 0) {
+        h->dense_next = 0;
+        h->sparse_next = 0;
+    }
+}
+
+__device__ __forceinline__ void block_card_add(unsigned long long card, unsigned long long* dst,
+                                               unsigned long long* part) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) card += __shfl_xor_sync(0xFFFFFFFFu, card, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = card;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        if (t) atomicAdd(dst, t);
+    }
+}
+
+template <int K, int G>
+__global__ void __launch_bounds__(kBatchThreads, 2)
+    dense_batch_kernel(BatchHeader* h, BatchPoolArgs pa) {
+    __shared__ unsigned long long item_s;
+    __shared__ unsigned long long part[kBatchThreads / 32];
+    const uint64_t ncols = (pa.words + 1) / 2;
+    const uint32_t nd = h->n_dense;
+    const uint64_t total = h->dense_items;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(&h->dense_next, 1ull);
+        __syncthreads();
+        const uint64_t item = item_s;
+        __syncthreads();
+        if (item >= total) break;
+        const uint64_t tile = item / nd;
+        const uint32_t qi = h->dense_list[item % nd];
+        const QueryDesc* d = h->desc + qi;
+        const uint64_t col = tile * kBatchThreads + threadIdx.x;
+        unsigned long long card = 0;
+        if (col < ncols) {
+            const Pred pred = d->pred;
+            uint64_t* out = d->out;
+            uint32_t P[4][K];
+            zero_planes<K>(P);
+            count_column<K, G>(P, pa.base + 2 * col, d->ids, d->n, pa.stride_words);
+            const bool vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
+            card = finish_column<K>(P, pred, pred.table, pa.r_bits, pa.words, out, col, vec_ok);
+        }
+        block_card_add(card, reinterpret_cast<unsigned long long*>(h->out_cards + qi), part);
+    }
+}
+
+__global__ void __launch_bounds__(kSparseBatchThreads, 1)
+    sparse_batch_kernel(BatchHeader* h, BatchPoolArgs pa) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ unsigned long long item_s;
+    __shared__ unsigned long long part[kSparseBatchThreads / 32];
+    uint32_t* tab = sm;                      // up to 2048 words (n <= 65535)
+    uint32_t* cnt = sm + 2048;               // 16-bit counters, two per word
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t nwarps = blockDim.x >> 5;
+    const uint32_t ns = h->n_sparse;
+    const uint64_t total = ns ? h->sparse_off[ns] : 0;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(&h->sparse_next, 1ull);
+        __syncthreads();
+        const uint64_t item = item_s;
+        __syncthreads();
+        if (item >= total) break;
+        // query of this item: last prefix entry <= item
+        uint32_t lo = 0, hi = ns;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) / 2;
+            if (h->sparse_off[mid] <= item)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const uint32_t qi = h->sparse_list[lo];
+        const QueryDesc* d = h->desc + qi;
+        const uint32_t n = d->n, tile_rows = d->tile_rows;
+        const uint64_t tile = item - h->sparse_off[lo];
+        const Pred pred = d->pred;
+        // truth table of f over 0..n
+        const uint32_t tab_words = (n + 1 + 31) / 32;
+        for (uint32_t w = threadIdx.x; w < tab_words; w += blockDim.x) {
+            uint32_t bits = 0;
+            if (pred.mode == 2) {
+                bits = pred.table[w];
+            } else {
+                for (uint32_t b = 0; b < 32; ++b) {
+                    const uint32_t c = w * 32 + b;
+                    if (c > n) break;
+                    uint32_t v = pred.v0;
+                    if (pred.mode == 1)
+#pragma unroll
+                        for (int i = 0; i < kMaxTransitions; ++i)
+                            if ((uint32_t)i < pred.ntrans) v ^= (c >= pred.trans[i]) ? 1u : 0u;
+                    bits |= v << b;
+                }
+            }
+            tab[w] = bits;
+        }
+        for (uint32_t i = threadIdx.x; i < tile_rows / 2; i += blockDim.x) cnt[i] = 0u;
+        __syncthreads();
+        const uint64_t rlo = tile * tile_rows;
+        const uint64_t rhi = min(rlo + tile_rows, pa.r_bits);
+        const uint32_t sub = tile_rows / kListTileRows;
+        const uint64_t t0 = tile * sub;
+        const uint64_t t1 = (t0 + sub < pa.tiles_per_list) ? t0 + sub : (uint64_t)pa.tiles_per_list;
+        for (uint32_t j = warp; j < n; j += nwarps) {
+            const uint32_t id = __ldg(d->ids + j);
+            const uint32_t* idx = pa.tile_index + (uint64_t)id * (pa.tiles_per_list + 1);
+            const uint32_t* pos = pa.positions + __ldg(pa.list_begin + id);
+            const uint32_t b = __ldg(idx + t0), e = __ldg(idx + t1);
+            for (uint32_t k = b + lane; k < e; k += 32) {
+                const uint32_t row = __ldg(pos + k) - (uint32_t)rlo;
+                atomicAdd(&cnt[row / 2], 1u << (16 * (row % 2)));
+            }
+        }
+        __syncthreads();
+        const uint32_t lanes = (uint32_t)((rhi - rlo + 31) / 32);
+        uint32_t* out32 = reinterpret_cast<uint32_t*>(d->out);
+        unsigned long long card = 0;
+        for (uint32_t l = threadIdx.x; l < lanes; l += blockDim.x) {
+            uint32_t o = 0;
+#pragma unroll
+            for (uint32_t w = 0; w < 16; ++w) {
+                const uint32_t word = cnt[l * 16 + w];
+                const uint32_t c0 = word & 0xFFFFu, c1 = word >> 16;
+                o |= ((tab[c0 >> 5] >> (c0 & 31u)) & 1u) << (2 * w);
+                o |= ((tab[c1 >> 5] >> (c1 & 31u)) & 1u) << (2 * w + 1);
+            }
+            const uint64_t row0 = rlo + 32ull * l;
+            if (row0 + 32 > pa.r_bits) o &= (1u << (pa.r_bits - row0)) - 1u;
+            out32[row0 / 32] = o;
+            card += __popc(o);
+        }
+        // the upper half of the last 64-bit word when r ends in its lower half
+        if (rhi == pa.r_bits && threadIdx.x == 0 && ((pa.r_bits + 31) / 32) % 2 == 1)
+            out32[(pa.r_bits + 31) / 32] = 0u;
+        block_card_add(card, reinterpret_cast<unsigned long long*>(h->out_cards + qi), part);
+        __syncthreads();
+    }
+}
+
+size_t sparse_batch_smem() { return (2048 + (size_t)kSparseMaxTile / 2) * 4; }
+
+}  // namespace
+
+// One descriptor slot: pinned host block, device block, completion event and
+// the graphs captured on it (one per counter-plane count).
+struct BatchSlot {
+    void* h = nullptr;
+    void* d = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool used = false;
+    std::map<int, cudaGraphExec_t> graphs;  // key: planes K * 16 + adder
+};
+
+struct BatchState {
+    static constexpr int kSlots = 3;
+    BatchSlot slots[kSlots];
+    int next = 0;
+    cudaStream_t capture = nullptr;
+    cudaStream_t infer = nullptr;
+    float* d_sel = nullptr;  // selector inference buffers
+    size_t sel_cap = 0;
+    DenseConfig cfg{0, kBatchThreads, 0, 2, 0};
+};
+
+void batch_state_free(bm_pool* p) {
+    BatchState* b = static_cast<BatchState*>(p->batch);
+    if (!b) return;
+    for (auto& sl : b->slots) {
+        for (auto& kv : sl.graphs) cudaGraphExecDestroy(kv.second);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.h) cudaFreeHost(sl.h);
+        if (sl.d) cudaFree(sl.d);
+    }
+    if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->infer) cudaStreamDestroy(b->infer);
+    if (b->d_sel) cudaFree(b->d_sel);
+    delete b;
+    p->batch = nullptr;
+}
+
+static BatchState* state(bm_pool* p) {
+    if (!p->batch) p->batch = new BatchState();
+    return static_cast<BatchState*>(p->batch);
+}
+
+static int slot_reserve(bm_pool* p, BatchSlot& sl, size_t bytes) {
+    if (sl.used) BM_CUDA_TRY(cudaEventSynchronize(sl.ev));
+    sl.used = false;
+    if (!sl.ev) BM_CUDA_TRY(cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming));
+    if (sl.cap >= bytes) return BM_OK;
+    for (auto& kv : sl.graphs) cudaGraphExecDestroy(kv.second);
+    sl.graphs.clear();
+    if (sl.h) cudaFreeHost(sl.h);
+    if (sl.d) {
+        cudaFree(sl.d);
+        p->device_bytes -= std::min<uint64_t>(p->device_bytes, sl.cap);
+    }
+    sl.h = sl.d = nullptr;
+    sl.cap = 0;
+    size_t cap = std::max<size_t>(bytes + bytes / 4, 1 << 20);
+    cap = (cap + 4095) & ~(size_t)4095;
+    if (cudaHostAlloc(&sl.h, cap, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        sl.h = nullptr;
+        return BM_ENOMEM;
+    }
+    int rc = track_alloc(p, &sl.d, cap);
+    if (rc) {
+        cudaFreeHost(sl.h);
+        sl.h = nullptr;
+        return rc;
+    }
+    sl.cap = cap;
+    return BM_OK;
+}
+
+static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, int adder,
+                     const BatchPoolArgs& pa, cudaGraphExec_t* out) {
+    const int key = K * 16 + adder;
+    auto it = sl.graphs.find(key);
+    if (it != sl.graphs.end()) {
+        *out = it->second;
+        return BM_OK;
+    }
+    if (!b->capture) BM_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
+    BatchHeader* h = static_cast<BatchHeader*>(sl.d);
+    const unsigned dense_grid = (unsigned)(p->sm_count * std::max(1, b->cfg.ctas_per_sm));
+    const unsigned sparse_grid = (unsigned)p->sm_count;
+    auto dense_fn = [&](auto fn) -> int {
+        BM_CUDA_TRY(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+        batch_zero_kernel<<<1, 256, 0, b->capture>>>(h);
+        fn<<<dense_grid, kBatchThreads, 0, b->capture>>>(h, pa);
+        sparse_batch_kernel<<<sparse_grid, kSparseBatchThreads, sparse_batch_smem(), b->capture>>>(
+            h, pa);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->capture, &g);
+        if (e != cudaSuccess) {
+            bm_note_cuda_error(e, "batch graph capture", __FILE__, __LINE__);
+            return BM_ECUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            bm_note_cuda_error(e, "batch graph instantiate", __FILE__, __LINE__);
+            return BM_ECUDA;
+        }
+        sl.graphs[key] = ex;
+        *out = ex;
+        return BM_OK;
+    };
+    BM_CUDA_TRY(cudaFuncSetAttribute(sparse_batch_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sparse_batch_smem()));
+    if (adder == 1) {
+        if (K <= 5) return dense_fn(dense_batch_kernel<5, 8>);
+        if (K <= 9) return dense_fn(dense_batch_kernel<9, 8>);
+        if (K <= 11) return dense_fn(dense_batch_kernel<11, 8>);
+        if (K <= 13) return dense_fn(dense_batch_kernel<13, 8>);
+        return dense_fn(dense_batch_kernel<17, 8>);
+    }
+    if (K <= 5) return dense_fn(dense_batch_kernel<5, 16>);
+    if (K <= 9) return dense_fn(dense_batch_kernel<9, 16>);
+    if (K <= 11) return dense_fn(dense_batch_kernel<11, 16>);
+    if (K <= 13) return dense_fn(dense_batch_kernel<13, 16>);
+    return dense_fn(dense_batch_kernel<17, 16>);
+}
+
+// Learned choices for every AUTO query of a batch, on the device.
+static int batch_select(bm_pool* p, BatchState* b, const std::vector<std::vector<float>>& feats,
+                        std::vector<int>& choice) {
+    const uint32_t B = (uint32_t)feats.size();
+    if (!B) return BM_OK;
+    const int F = kFeatures, H = kHidden, C = kCandidates;
+    const size_t np = mlp_param_count(F, H, C);
+    const size_t need = np + (size_t)B * (F + 2 * H + C);
+    if (!b->infer) BM_CUDA_TRY(cudaStreamCreateWithFlags(&b->infer, cudaStreamNonBlocking));
+    if (b->sel_cap < need) {
+        if (b->d_sel) {
+            cudaFree(b->d_sel);
+            p->device_bytes -= std::min<uint64_t>(p->device_bytes, b->sel_cap * 4);
+        }
+        b->d_sel = nullptr;
+        b->sel_cap = 0;
+        int rc = track_alloc(p, (void**)&b->d_sel, need * 4);
+        if (rc) return rc;
+        b->sel_cap = need;
+    }
+    std::vector<float> x((size_t)B * F), y((size_t)B * C);
+    for (uint32_t i = 0; i < B; ++i)
+        for (int f = 0; f < F; ++f) x[(size_t)i * F + f] = (feats[i][f] - p->sel_mean[f]) / p->sel_std[f];
+    float* dP = b->d_sel;
+    float* dx = dP + np;
+    float* dh1 = dx + (size_t)B * F;
+    float* dh2 = dh1 + (size_t)B * H;
+    float* dy = dh2 + (size_t)B * H;
+    BM_CUDA_TRY(cudaMemcpyAsync(dP, p->sel_params.data(), np * 4, cudaMemcpyHostToDevice, b->infer));
+    BM_CUDA_TRY(cudaMemcpyAsync(dx, x.data(), x.size() * 4, cudaMemcpyHostToDevice, b->infer));
+    int rc = bm_mlp_forward(dP, F, H, C, dx, B, dh1, dh2, dy, b->infer);
+    if (rc) return rc;
+    BM_CUDA_TRY(cudaMemcpyAsync(y.data(), dy, y.size() * 4, cudaMemcpyDeviceToHost, b->infer));
+    BM_CUDA_TRY(cudaStreamSynchronize(b->infer));
+    choice.resize(B);
+    for (uint32_t i = 0; i < B; ++i) {
+        int best = 0;
+        for (int c = 1; c < C; ++c)
+            if (y[(size_t)i * C + c] < y[(size_t)i * C + best]) best = c;
+        choice[i] = best;
+    }
+    return BM_OK;
+}
+
+}  // namespace bm
+
+using namespace bm;
+
+extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, uint64_t* out_cards,
+                                  int32_t* chosen_paths, void* stream) {
+    if (!p || !q || nq == 0 || !out_cards) return BM_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    BM_CUDA_TRY(cudaSetDevice(p->device));
+    BatchState* b = state(p);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // validate, truth tables, candidate choice
+    std::vector<std::vector<uint8_t>> truth(nq);
+    std::vector<Candidate> cand(nq);
+    std::vector<uint32_t> auto_idx;
+    std::vector<std::vector<float>> feats;
+    uint64_t total_ids = 0, total_tab = 0;
+    uint32_t max_dense_n = 1;
+    for (uint32_t i = 0; i < nq; ++i) {
+        const bm_query& qi = q[i];
+        if (!qi.out_words || qi.reserved || qi.path < BM_PATH_AUTO || qi.path > BM_PATH_SPARSE)
+            return BM_EINVAL;
+        int rc = validate_ids(p, qi.ids, qi.n, qi.path);
+        if (!rc) rc = query_truth(&qi, truth[i]);
+        if (rc) return rc;
+        total_ids += qi.n;
+        if (qi.path == BM_PATH_AUTO) {
+            if (!p->sel_params.empty() && p->sel_outputs == kCandidates) {
+                auto_idx.push_back(i);
+                feats.emplace_back(kFeatures);
+                query_features(p, qi.ids, qi.n, truth[i], feats.back().data());
+            } else {
+                cand[i] = rule_choice(p, qi.ids, qi.n);
+            }
+        } else {
+            cand[i] = Candidate{qi.path, qi.path == BM_PATH_SPARSE ? p->sparse_cfg.tile_rows : 0u};
+        }
+    }
+    if (!auto_idx.empty()) {
+        std::vector<int> choice;
+        int rc = batch_select(p, b, feats, choice);
+        if (rc) return rc;
+        for (size_t j = 0; j < auto_idx.size(); ++j) {
+            const uint32_t i = auto_idx[j];
+            Candidate c = kCandidateTable[choice[j]];
+            // a candidate whose inputs are missing falls back to the one that exists
+            bool lists = true, dense = true;
+            for (uint32_t k = 0; k < q[i].n; ++k) {
+                lists = lists && p->list_present[q[i].ids[k]];
+                dense = dense && p->dense_present[q[i].ids[k]];
+            }
+            if (c.path == BM_PATH_SPARSE && !lists) c = kCandidateTable[0];
+            if (c.path == BM_PATH_DENSE && !dense) c = Candidate{BM_PATH_SPARSE, p->sparse_cfg.tile_rows};
+            cand[i] = c;
+        }
+    }
+    std::vector<Pred> preds(nq);
+    std::vector<uint32_t> dense_list, sparse_list;
+    std::vector<uint64_t> sparse_off(1, 0);
+    for (uint32_t i = 0; i < nq; ++i) {
+        preds[i] = compile_pred(truth[i].data(), q[i].n);
+        if (preds[i].mode == 2) total_tab += preds[i].table_words32;
+        if (cand[i].path == BM_PATH_SPARSE) {
+            if (cand[i].tile_rows > kSparseMaxTile) cand[i].tile_rows = kSparseMaxTile;
+            sparse_list.push_back(i);
+            sparse_off.push_back(sparse_off.back() +
+                                 (p->r_bits + cand[i].tile_rows - 1) / cand[i].tile_rows);
+        } else {
+            dense_list.push_back(i);
+            max_dense_n = std::max(max_dense_n, q[i].n);
+        }
+        if (chosen_paths) chosen_paths[i] = cand[i].path;
+    }
+
+    // descriptor block: header | descs | dense list | sparse list | sparse off | ids | tables
+    auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    const size_t o_desc = al(sizeof(BatchHeader));
+    const size_t o_dl = o_desc + al(sizeof(QueryDesc) * nq);
+    const size_t o_sl = o_dl + al(4 * dense_list.size());
+    const size_t o_so = o_sl + al(4 * sparse_list.size());
+    const size_t o_ids = o_so + al(8 * sparse_off.size());
+    const size_t o_tab = o_ids + al(4 * total_ids);
+    const size_t bytes = o_tab + al(4 * total_tab);
+    BatchSlot& sl = b->slots[b->next];
+    b->next = (b->next + 1) % BatchState::kSlots;
+    int rc = slot_reserve(p, sl, bytes);
+    if (rc) return rc;
+    uint8_t* hb = static_cast<uint8_t*>(sl.h);
+    uint8_t* db = static_cast<uint8_t*>(sl.d);
+    BatchHeader* hh = reinterpret_cast<BatchHeader*>(hb);
+    memset(hh, 0, sizeof(BatchHeader));
+    hh->out_cards = out_cards;
+    hh->desc = reinterpret_cast<const QueryDesc*>(db + o_desc);
+    hh->dense_list = reinterpret_cast<const uint32_t*>(db + o_dl);
+    hh->sparse_list = reinterpret_cast<const uint32_t*>(db + o_sl);
+    hh->sparse_off = reinterpret_cast<const uint64_t*>(db + o_so);
+    hh->nq = nq;
+    hh->n_dense = (uint32_t)dense_list.size();
+    hh->n_sparse = (uint32_t)sparse_list.size();
+    const uint64_t ncols = (p->words + 1) / 2;
+    const uint64_t dense_tiles = (ncols + kBatchThreads - 1) / kBatchThreads;
+    hh->dense_items = dense_tiles * dense_list.size();
+    QueryDesc* hd = reinterpret_cast<QueryDesc*>(hb + o_desc);
+    uint32_t* hids = reinterpret_cast<uint32_t*>(hb + o_ids);
+    uint32_t* htab = reinterpret_cast<uint32_t*>(hb + o_tab);
+    uint64_t id_pos = 0, tab_pos = 0;
+    for (uint32_t i = 0; i < nq; ++i) {
+        memcpy(hids + id_pos, q[i].ids, 4ull * q[i].n);
+        hd[i].ids = reinterpret_cast<const uint32_t*>(db + o_ids) + id_pos;
+        hd[i].n = q[i].n;
+        hd[i].tile_rows = cand[i].tile_rows;
+        hd[i].out = q[i].out_words;
+        hd[i].pred = preds[i];
+        if (preds[i].mode == 2) {
+            uint32_t* t = htab + tab_pos;
+            memset(t, 0, 4ull * preds[i].table_words32);
+            for (uint32_t c = 0; c <= q[i].n; ++c)
+                if (truth[i][c]) t[c >> 5] |= 1u << (c & 31);
+            hd[i].pred.table = reinterpret_cast<const uint32_t*>(db + o_tab) + tab_pos;
+            tab_pos += preds[i].table_words32;
+        }
+        id_pos += q[i].n;
+    }
+    if (!dense_list.empty())
+        memcpy(hb + o_dl, dense_list.data(), 4 * dense_list.size());
+    if (!sparse_list.empty())
+        memcpy(hb + o_sl, sparse_list.data(), 4 * sparse_list.size());
+    memcpy(hb + o_so, sparse_off.data(), 8 * sparse_off.size());
+
+    BatchPoolArgs pa{};
+    pa.base = p->d_dense;
+    pa.stride_words = p->stride_words;
+    pa.words = p->words;
+    pa.r_bits = p->r_bits;
+    pa.positions = p->d_pos;
+    pa.list_begin = p->d_list_begin;
+    pa.tile_index = p->d_tile_index;
+    pa.tiles_per_list = p->tiles_per_list;
+    const int K = planes_for(max_dense_n);
+    const int kk = K <= 5 ? 5 : K <= 9 ? 9 : K <= 11 ? 11 : K <= 13 ? 13 : 17;
+    cudaGraphExec_t ex = nullptr;
+    rc = graph_for(p, b, sl, kk, b->cfg.adder, pa, &ex);
+    if (rc) return rc;
+    BM_CUDA_TRY(cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, s));
+    BM_CUDA_TRY(cudaGraphLaunch(ex, s));
+    BM_CUDA_TRY(cudaEventRecord(sl.ev, s));
+    sl.used = true;
+    return BM_OK;
+}
+
+extern "C" int bm_pool_set_batch_config(bm_pool* p, int ctas_per_sm, int adder) {
+    if (!p || ctas_per_sm < 1 || ctas_per_sm > 2 || adder < 0 || adder > 1) return BM_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    BatchState* b = state(p);
+    if (b->cfg.ctas_per_sm != ctas_per_sm || b->cfg.adder != adder) {
+        for (auto& sl : b->slots) {
+            if (sl.used) cudaEventSynchronize(sl.ev);
+            for (auto& kv : sl.graphs) cudaGraphExecDestroy(kv.second);
+            sl.graphs.clear();
+        }
+    }
+    b->cfg.ctas_per_sm = ctas_per_sm;
+    b->cfg.adder = adder;
+    return BM_OK;
+}

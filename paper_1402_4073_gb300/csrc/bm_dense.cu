@@ -21,7 +21,7 @@
 //    recycled through a second mbarrier per stage.  All waits are bounded.
 #include <algorithm>
 
-#include "bm_device.cuh"
+#include "bm_dense_common.cuh"
 
 namespace bm {
 
@@ -35,84 +35,6 @@ namespace {
 
 using namespace dev;
 
-// Per-lane accumulation of a partial group (nb < 16 inputs) read by `get(b)`.
-template <int K, typename Get>
-__device__ __forceinline__ void add_partial(uint32_t (&P)[4][K], uint32_t nb, Get get) {
-    uint32_t b = 0;
-    for (; b + 2 <= nb; b += 2) {
-        uint4 u = get(b), v = get(b + 1);
-        add2<K>(P[0], u.x, v.x);
-        add2<K>(P[1], u.y, v.y);
-        add2<K>(P[2], u.z, v.z);
-        add2<K>(P[3], u.w, v.w);
-    }
-    if (b < nb) {
-        uint4 u = get(b);
-        add1<K>(P[0], u.x);
-        add1<K>(P[1], u.y);
-        add1<K>(P[2], u.z);
-        add1<K>(P[3], u.w);
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void add_group16(uint32_t (&P)[4][K], const uint4 (&v)[16]) {
-    uint32_t x[16];
-#pragma unroll
-    for (int b = 0; b < 16; ++b) x[b] = v[b].x;
-    add16<K>(P[0], x);
-#pragma unroll
-    for (int b = 0; b < 16; ++b) x[b] = v[b].y;
-    add16<K>(P[1], x);
-#pragma unroll
-    for (int b = 0; b < 16; ++b) x[b] = v[b].z;
-    add16<K>(P[2], x);
-#pragma unroll
-    for (int b = 0; b < 16; ++b) x[b] = v[b].w;
-    add16<K>(P[3], x);
-}
-
-// Predicate, tail mask, store and popcount of one 128-row column.
-template <int K>
-__device__ __forceinline__ uint32_t finish_column(const uint32_t (&P)[4][K], const DenseArgs& a,
-                                                  const uint32_t* tab, uint64_t col, bool vec_ok) {
-    uint32_t o0 = eval_pred<K>(P[0], a.pred, tab);
-    uint32_t o1 = eval_pred<K>(P[1], a.pred, tab);
-    uint32_t o2 = eval_pred<K>(P[2], a.pred, tab);
-    uint32_t o3 = eval_pred<K>(P[3], a.pred, tab);
-    uint64_t w0 = (uint64_t)o0 | ((uint64_t)o1 << 32);
-    uint64_t w1 = (uint64_t)o2 | ((uint64_t)o3 << 32);
-    const uint64_t i0 = 2 * col, i1 = i0 + 1;
-    const uint32_t tail = (uint32_t)(a.r_bits & 63u);
-    const uint64_t last = a.words - 1;
-    if (tail) {
-        const uint64_t m = (1ull << tail) - 1ull;
-        if (i0 == last) w0 &= m;
-        if (i1 == last) w1 &= m;
-    }
-    if (i1 < a.words) {
-        if (vec_ok) {
-            asm volatile("st.global.v2.u64 [%0], {%1, %2};" ::"l"(a.out + i0), "l"(w0), "l"(w1)
-                         : "memory");
-        } else {
-            a.out[i0] = w0;
-            a.out[i1] = w1;
-        }
-        return (uint32_t)(__popcll(w0) + __popcll(w1));
-    }
-    if (i0 < a.words) {
-        a.out[i0] = w0;
-        return (uint32_t)__popcll(w0);
-    }
-    return 0;
-}
-
-__device__ __forceinline__ void flush_card(unsigned long long card, unsigned long long* out) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) card += __shfl_xor_sync(0xFFFFFFFFu, card, o);
-    if ((threadIdx.x & 31) == 0 && out && card) atomicAdd(out, card);
-}
-
 __device__ __forceinline__ void load_table(const DenseArgs& a, uint32_t* tab, int tid, int nthr) {
     if (a.pred.mode == 2)
         for (uint32_t i = tid; i < a.pred.table_words32; i += nthr) tab[i] = a.pred.table[i];
@@ -121,7 +43,7 @@ __device__ __forceinline__ void load_table(const DenseArgs& a, uint32_t* tab, in
 // ---------------------------------------------------------------------------
 // variant 0: direct streaming loads
 
-template <int K>
+template <int K, int G>
 __global__ void __launch_bounds__(256, (K <= 13 ? 2 : 1)) csa_direct_kernel(DenseArgs a) {
     extern __shared__ uint32_t tab[];
     load_table(a, tab, threadIdx.x, blockDim.x);
@@ -132,26 +54,9 @@ __global__ void __launch_bounds__(256, (K <= 13 ? 2 : 1)) csa_direct_kernel(Dens
     for (uint64_t col = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; col < ncols;
          col += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t P[4][K];
-#pragma unroll
-        for (int l = 0; l < 4; ++l)
-#pragma unroll
-            for (int j = 0; j < K; ++j) P[l][j] = 0u;
-        const uint64_t* colbase = a.base + 2 * col;
-        uint32_t k = 0;
-        for (; k + 16 <= a.n; k += 16) {
-            uint4 v[16];
-#pragma unroll
-            for (int b = 0; b < 16; ++b)
-                v[b] = ld_stream(colbase + (uint64_t)__ldg(a.ids + k + b) * a.stride_words);
-            add_group16<K>(P, v);
-        }
-        if (k < a.n) {
-            const uint32_t* ids = a.ids + k;
-            add_partial<K>(P, a.n - k, [&](uint32_t b) {
-                return ld_stream(colbase + (uint64_t)__ldg(ids + b) * a.stride_words);
-            });
-        }
-        card += finish_column<K>(P, a, tab, col, vec_ok);
+        zero_planes<K>(P);
+        count_column<K, G>(P, a.base + 2 * col, a.ids, a.n, a.stride_words);
+        card += finish_column<K>(P, a.pred, tab, a.r_bits, a.words, a.out, col, vec_ok);
     }
     flush_card(card, a.card);
 }
@@ -251,7 +156,8 @@ __global__ void __launch_bounds__(NT + 32, 1) csa_bulk_kernel(DenseArgs a, int s
         }
         if (!ok) break;
         const uint64_t col = tile * NT + tid;
-        if (col < ncols) card += finish_column<K>(P, a, tab, col, vec_ok);
+        if (col < ncols)
+            card += finish_column<K>(P, a.pred, tab, a.r_bits, a.words, a.out, col, vec_ok);
     }
     if (ok) flush_card(card, a.card);
 }
@@ -265,7 +171,7 @@ int launch_k(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStrea
         const uint64_t blocks_needed = (ncols + threads - 1) / threads;
         const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);
         const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(blocks_needed, cap));
-        auto fn = csa_direct_kernel<K>;
+        auto fn = cfg.adder == 1 ? csa_direct_kernel<K, 8> : csa_direct_kernel<K, 16>;
         if (tab_bytes > 48 * 1024)
             BM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)tab_bytes));

@@ -84,6 +84,21 @@ __device__ __forceinline__ void add16(uint32_t (&P)[K], const uint32_t (&x)[16])
     ripple<K>(P, sixteens, 4);
 }
 
+// Add eight input words: 7 full adders with planes 0..2 as carry-save
+// accumulators, the weight-8 carry rippled into planes 3.. .  Requires K >= 4.
+template <int K>
+__device__ __forceinline__ void add8(uint32_t (&P)[K], const uint32_t (&x)[8]) {
+    uint32_t twosA, twosB, foursA, foursB, eights;
+    csa(twosA, P[0], P[0], x[0], x[1]);
+    csa(twosB, P[0], P[0], x[2], x[3]);
+    csa(foursA, P[1], P[1], twosA, twosB);
+    csa(twosA, P[0], P[0], x[4], x[5]);
+    csa(twosB, P[0], P[0], x[6], x[7]);
+    csa(foursB, P[1], P[1], twosA, twosB);
+    csa(eights, P[2], P[2], foursA, foursB);
+    ripple<K>(P, eights, 3);
+}
+
 // [count > a] for each of 32 rows, a < 2^K (Sec. 4.3 comparator against a
 // constant, with the constant's bits read at run time; they are the same
 // in every thread, so the branches are uniform): scanning bits from the top,

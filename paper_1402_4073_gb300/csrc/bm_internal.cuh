@@ -75,9 +75,33 @@ struct DenseConfig {
     int threads;   // consumer threads per CTA
     int stages;    // pipeline depth (variant 1)
     int ctas_per_sm;
+    int adder = 0;  // sideways-sum block: 0 = 16 inputs, 1 = 8 inputs (variant 0)
 };
 
 int launch_dense(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStream_t s);
+
+// Arguments of one sparse (ScanCount) query launch.
+struct SparseArgs {
+    const uint32_t* positions;   // pool list arena
+    const uint64_t* list_begin;  // device, per id: first entry in the arena
+    const uint32_t* tile_index;  // device, per id: tiles_per_list + 1 entries
+    uint32_t tiles_per_list;     // ceil(r / kListTileRows)
+    uint32_t tile_rows;          // rows per CTA tile, a multiple of kListTileRows
+    uint64_t r_bits;
+    const uint32_t* ids;         // device, n ids
+    uint32_t n;
+    Pred pred;
+    uint64_t* out;
+    unsigned long long* card;
+};
+
+struct SparseConfig {
+    uint32_t tile_rows;  // multiple of kListTileRows
+    int threads;
+    int ctas_per_sm;
+};
+
+int launch_sparse(const SparseArgs& a, const SparseConfig& cfg, int sm_count, cudaStream_t s);
 int launch_cardinality(const uint64_t* words, uint64_t r_bits, unsigned long long* out,
                        int sm_count, cudaStream_t s);
 int planes_for(uint32_t n);  // counter planes needed for counts 0..n
@@ -118,14 +142,25 @@ struct bm_pool {
     bm_stage_slot slots[kSlots];
     int next_slot = 0;
     bm::DenseConfig dense_cfg{0, 256, 4, 2};
+    bm::SparseConfig sparse_cfg{32768, 512, 2};
+    // learned selector (empty: fixed density rule)
+    std::vector<float> sel_params;
+    float sel_mean[8] = {}, sel_std[8] = {};
+    int sel_outputs = 0;
+    void* batch = nullptr;  // batched-query state (descriptor slots, graphs)
     std::mutex mu;
 };
 
 namespace bm {
+// Truth table f(0..n) of a query descriptor.
+int query_truth(const bm_query* q, std::vector<uint8_t>& f);
+// Host validation of ids for a path (BM_PATH_*).
+int validate_ids(const bm_pool* p, const uint32_t* ids, uint32_t n, int path);
 // Reserve a staging slot of at least `bytes`, waiting for its previous use.
 int stage_acquire(bm_pool* p, size_t bytes, bm_stage_slot** out);
 // Copy the slot's first `bytes` to the device on `s` and mark its reuse point.
 int stage_commit(bm_stage_slot* slot, size_t bytes, cudaStream_t s);
 int stage_release(bm_stage_slot* slot, cudaStream_t s);
 int track_alloc(bm_pool* p, void** ptr, size_t bytes);
+void batch_state_free(bm_pool* p);
 }  // namespace bm

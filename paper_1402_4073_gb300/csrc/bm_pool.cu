@@ -191,6 +191,7 @@ int bm_pool_destroy(bm_pool* p) {
     if (!p) return BM_OK;
     cudaSetDevice(p->device);
     cudaDeviceSynchronize();
+    batch_state_free(p);
     for (auto& sl : p->slots) {
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.h) cudaFreeHost(sl.h);
@@ -334,12 +335,14 @@ int bm_pool_info(const bm_pool* p, bm_pool_info_t* out) {
     return BM_OK;
 }
 
-int bm_pool_set_dense_config(bm_pool* p, int variant, int threads, int stages, int ctas_per_sm) {
+int bm_pool_set_dense_config(bm_pool* p, int variant, int threads, int stages, int ctas_per_sm,
+                             int adder) {
     if (!p || variant < 0 || variant > 1 || ctas_per_sm < 1 || ctas_per_sm > 8) return BM_EINVAL;
+    if (adder < 0 || adder > 1 || (variant == 1 && adder != 0)) return BM_EINVAL;
     if (variant == 1 && (!(threads == 64 || threads == 128) || stages < 2 || stages > 8))
         return BM_EINVAL;
     std::lock_guard<std::mutex> lk(p->mu);
-    p->dense_cfg = DenseConfig{variant, variant == 0 ? 256 : threads, stages, ctas_per_sm};
+    p->dense_cfg = DenseConfig{variant, variant == 0 ? 256 : threads, stages, ctas_per_sm, adder};
     return BM_OK;
 }
 

@@ -1,0 +1,94 @@
+// Per-query kernel choice: features, fixed rule, learned selector.
+#include <cmath>
+
+#include "bm_select.h"
+
+namespace bm {
+
+const Candidate kCandidateTable[kCandidates] = {
+    {BM_PATH_DENSE, 0}, {BM_PATH_SPARSE, 16384}, {BM_PATH_SPARSE, 32768}, {BM_PATH_SPARSE, 65536}};
+
+void query_features(const bm_pool* p, const uint32_t* ids, uint32_t n,
+                    const std::vector<uint8_t>& f, float out[kFeatures]) {
+    double sum = 0.0, mx = 0.0;
+    for (uint32_t k = 0; k < n; ++k) {
+        const double d = (double)p->card[ids[k]] / (double)p->r_bits;
+        sum += d;
+        mx = d > mx ? d : mx;
+    }
+    uint32_t first = 0;  // first count where f changes (0 if f is constant)
+    for (uint32_t c = 1; c <= n; ++c)
+        if ((f[c] != 0) != (f[c - 1] != 0)) {
+            first = c;
+            break;
+        }
+    out[0] = (float)std::log2((double)n);
+    out[1] = (float)((double)first / (double)n);
+    out[2] = (float)std::log10(std::max(sum / n, 1e-9));
+    out[3] = (float)std::log10(std::max(mx, 1e-9));
+    out[4] = (float)std::log2((double)p->r_bits);
+}
+
+static bool all_have(const std::vector<uint8_t>& present, const uint32_t* ids, uint32_t n) {
+    for (uint32_t k = 0; k < n; ++k)
+        if (!present[ids[k]]) return false;
+    return true;
+}
+
+Candidate rule_choice(const bm_pool* p, const uint32_t* ids, uint32_t n) {
+    const bool lists = all_have(p->list_present, ids, n);
+    const bool dense = all_have(p->dense_present, ids, n);
+    if (!lists) return kCandidateTable[0];
+    uint64_t b = 0;
+    for (uint32_t k = 0; k < n; ++k) b += p->list_len[ids[k]];
+    const double dense_bytes = (double)n * (double)p->r_bits / 8.0;
+    if (!dense || 4.0 * 4.0 * (double)b < dense_bytes)
+        return Candidate{BM_PATH_SPARSE, p->sparse_cfg.tile_rows};
+    return kCandidateTable[0];
+}
+
+void mlp_forward_host(const float* P, int C, const float* x, float* y) {
+    const int F = kFeatures, H = kHidden;
+    const float* W1 = P;
+    const float* b1 = W1 + F * H;
+    const float* W2 = b1 + H;
+    const float* b2 = W2 + H * H;
+    const float* W3 = b2 + H;
+    const float* b3 = W3 + H * C;
+    float h1[kHidden], h2[kHidden];
+    for (int j = 0; j < H; ++j) {
+        float s = b1[j];
+        for (int i = 0; i < F; ++i) s += x[i] * W1[i * H + j];
+        h1[j] = s > 0.f ? s : 0.f;
+    }
+    for (int j = 0; j < H; ++j) {
+        float s = b2[j];
+        for (int i = 0; i < H; ++i) s += h1[i] * W2[i * H + j];
+        h2[j] = s > 0.f ? s : 0.f;
+    }
+    for (int j = 0; j < C; ++j) {
+        float s = b3[j];
+        for (int i = 0; i < H; ++i) s += h2[i] * W3[i * C + j];
+        y[j] = s;
+    }
+}
+
+Candidate select_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
+                           const std::vector<uint8_t>& f) {
+    if (p->sel_params.empty() || p->sel_outputs != kCandidates) return rule_choice(p, ids, n);
+    const bool lists = all_have(p->list_present, ids, n);
+    const bool dense = all_have(p->dense_present, ids, n);
+    float x[kFeatures], y[kCandidates];
+    query_features(p, ids, n, f, x);
+    for (int i = 0; i < kFeatures; ++i) x[i] = (x[i] - p->sel_mean[i]) / p->sel_std[i];
+    mlp_forward_host(p->sel_params.data(), kCandidates, x, y);
+    int best = -1;
+    for (int c = 0; c < kCandidates; ++c) {
+        const Candidate& k = kCandidateTable[c];
+        if ((k.path == BM_PATH_DENSE && !dense) || (k.path == BM_PATH_SPARSE && !lists)) continue;
+        if (best < 0 || y[c] < y[best]) best = c;
+    }
+    return best < 0 ? kCandidateTable[0] : kCandidateTable[best];
+}
+
+}  // namespace bm

@@ -1,0 +1,46 @@
+// Kernel selection per query: query features, the fixed density rule, and
+// the learned selector (a small MLP predicting each candidate's log time).
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "bm_internal.cuh"
+
+namespace bm {
+
+constexpr int kFeatures = 5;
+constexpr int kHidden = 64;
+
+// The kernel configurations a query can run on (the selector's outputs).
+struct Candidate {
+    int path;            // BM_PATH_DENSE or BM_PATH_SPARSE
+    uint32_t tile_rows;  // sparse tile (0 for dense)
+};
+constexpr int kCandidates = 4;
+extern const Candidate kCandidateTable[kCandidates];
+
+// Features of a query: log2 n, first transition of f over n, log10 of the
+// mean and of the largest input density, log2 r.
+void query_features(const bm_pool* p, const uint32_t* ids, uint32_t n,
+                    const std::vector<uint8_t>& f, float out[kFeatures]);
+
+// Fixed rule: ScanCount when every input has a position list and the lists
+// are at least 128x smaller than the dense words (mean density < 1/128),
+// else the dense counter.
+Candidate rule_choice(const bm_pool* p, const uint32_t* ids, uint32_t n);
+
+// Learned choice if a selector is installed, else the rule; candidates whose
+// inputs are missing (no lists, no dense words) are never chosen.
+Candidate select_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
+                           const std::vector<uint8_t>& f);
+
+// MLP forward on the host for one feature vector (fp32), all C outputs.
+void mlp_forward_host(const float* params, int C, const float* x, float* y);
+
+inline size_t mlp_param_count(int F, int H, int C) {
+    return (size_t)F * H + H + (size_t)H * H + H + (size_t)H * C + C;
+}
+
+}  // namespace bm

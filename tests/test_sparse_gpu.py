@@ -1,0 +1,145 @@
+"""GPU parity of the ScanCount kernel over sorted position lists, and of the
+single-query path choice, against the CPU oracle (bit-exact)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bm():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1402_4073_gb300 as bm
+    return bm
+
+
+def _run(bm, pool, q, path):
+    out = pool.empty_words()
+    out.fill_(-1)
+    card = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    chosen = bm.query_run(pool, q, out, card, path=path)
+    torch.cuda.synchronize()
+    pool.status()
+    return (bm.to_numpy_words(out), int(card.item())), chosen
+
+
+def _eq(got, want, what=""):
+    assert np.array_equal(got[0], want[0]), f"{what}: words differ"
+    assert got[1] == want[1], f"{what}: card {got[1]} != {want[1]}"
+
+
+def _pool(bm, dg, r_bits, dens, stream, lists=True):
+    words = dg.bernoulli(stream, r_bits, dens)
+    flat, offs = dg.positions(words, r_bits)
+    pool = bm.Pool(r_bits, words.shape[0])
+    pool.put_dense(words)
+    if lists:
+        pool.put_positions(flat, offs)
+    return pool, words, flat, offs
+
+
+@pytest.mark.parametrize("tile", [8192, 16384, 32768, 65536])
+@pytest.mark.parametrize("r_bits", [1, 100, 8192, 8193, 65536 * 3 + 77, 1 << 20])
+def test_scancount_tiles_and_ragged_rows(bm, oracle_lib, dg, tile, r_bits):
+    dens = np.array([1e-3, 1e-2, 0.05, 0.3, 0.0, 1.0, 2e-3, 0.5])
+    pool, words, flat, offs = _pool(bm, dg, r_bits, dens, dg.STREAM_TESTS + 11000)
+    with pool:
+        pool.set_sparse_config(tile, 512, 2)
+        ids = np.array([0, 1, 2, 3, 4, 5, 6, 7, 2, 2], dtype=np.uint32)  # repeats
+        for theta in (0, 1, 2, 3, 5, 10, 11):
+            q = dg.Query(ids, 0, theta=theta)
+            got, path = _run(bm, pool, q, bm.PATH_SPARSE)
+            assert path == bm.PATH_SPARSE
+            _eq(got, oracle_lib.scancount(flat, offs, ids, r_bits, theta), f"theta={theta}")
+            _eq(got, oracle_lib.query(words, q, r_bits), f"dense view theta={theta}")
+        q = dg.Query(ids, 1, lo=2, hi=4)
+        got, _ = _run(bm, pool, q, bm.PATH_SPARSE)
+        _eq(got, oracle_lib.query(words, q, r_bits), "interval")
+
+
+@pytest.mark.parametrize("N", [2, 255, 256, 300, 4096])
+def test_scancount_counter_width(bm, oracle_lib, dg, N):
+    """8-bit counters up to N = 255, 16-bit above; planted rows reach count N."""
+    r_bits = 1 << 17
+    pool_n = min(N, 600)
+    dens = dg.log_uniform(dg.uniform(dg.STREAM_TESTS + 11100, pool_n), 1e-4, 2e-2)
+    words = dg.bernoulli(dg.STREAM_TESTS + 11101, r_bits, dens)
+    words[:, 5] |= np.uint64(0xF0F0)  # rows where every input is set
+    ids = (np.arange(N) % pool_n).astype(np.uint32)
+    flat, offs = dg.positions(words, r_bits)
+    with bm.Pool(r_bits, pool_n) as pool:
+        pool.put_dense(words)
+        pool.put_positions(flat, offs)
+        for theta in (1, 2, N // 2, N - 1, N, N + 1):
+            q = dg.Query(ids, 0, theta=max(theta, 0))
+            got, _ = _run(bm, pool, q, bm.PATH_SPARSE)
+            want = oracle_lib.query(words, q, r_bits)
+            _eq(got, want, f"N={N} theta={theta}")
+        f = np.zeros(N + 1, bool)
+        f[::3] = True
+        f[N] = True
+        q = dg.Query(ids, 2, table=dg.table_from_bools(f))
+        got, _ = _run(bm, pool, q, bm.PATH_SPARSE)
+        _eq(got, oracle_lib.query(words, q, r_bits), "table")
+
+
+def test_sparse_workload_subset(bm, oracle_lib, dg):
+    """Scaled sparse workload: 300 bitmaps, r = 2^20, densities log-uniform in
+    [1e-5, 1e-2], queries with N log-uniform in [2, 300], theta <= min(N, 64),
+    on every path, against the oracle."""
+    r_bits = 1 << 20
+    d = dg.pool_densities(dg.STREAM_TESTS + 11200, 300, 1e-5, 1e-2)
+    words = dg.bernoulli(dg.STREAM_TESTS + 11201, r_bits, d)
+    flat, offs = dg.positions(words, r_bits)
+    queries = dg.sparse_queries(12, pool=300, nmax=300, stream=dg.STREAM_TESTS + 11202)
+    with bm.Pool(r_bits, 300) as pool:
+        pool.put_dense(words)
+        pool.put_positions(flat, offs)
+        for q in queries:
+            want = oracle_lib.query(words, q, r_bits)
+            for path in (bm.PATH_DENSE, bm.PATH_SPARSE, bm.PATH_AUTO):
+                got, chosen = _run(bm, pool, q, path)
+                _eq(got, want, f"n={q.n} path={path}")
+                assert chosen in (bm.PATH_DENSE, bm.PATH_SPARSE)
+
+
+def test_lists_from_device_and_validation(bm, dg):
+    r_bits = 50000
+    words = dg.bernoulli(dg.STREAM_TESTS + 11300, r_bits, np.array([0.01, 0.02, 0.03]))
+    flat, offs = dg.positions(words, r_bits)
+    with bm.Pool(r_bits, 4) as pool:
+        pool.put_dense(words)
+        pool.put_positions(torch.from_numpy(flat.view(np.int32)).cuda(), offs)
+        assert pool.info()["lists_loaded"] == 3
+        q = dg.Query(np.array([0, 1, 2]), 0, theta=1)
+        out = pool.empty_words()
+        bm.query_run(pool, q, out, path=bm.PATH_SPARSE)
+        a = bm.to_numpy_words(out)
+        assert np.array_equal(a, words[0] | words[1] | words[2])
+        # id 3 has no list: the sparse path is refused, AUTO uses dense (absent too -> error)
+        with pytest.raises(bm.BMError) as e:
+            bm.query_run(pool, dg.Query(np.array([0, 3]), 0, theta=1), out, path=bm.PATH_SPARSE)
+        assert e.value.code == bm.BM_ERANGE
+        # unsorted or out-of-range lists are refused (host and device input)
+        bad = np.array([5, 3], dtype=np.uint32)
+        with pytest.raises(bm.BMError):
+            pool.put_positions(bad, np.array([0, 2]), first_id=3)
+        with pytest.raises(bm.BMError):
+            pool.put_positions(torch.tensor([1, r_bits], dtype=torch.int32, device="cuda"),
+                               np.array([0, 2]), first_id=3)
+        with pytest.raises(bm.BMError):
+            pool.set_sparse_config(10000, 512, 2)
+
+
+def test_auto_rule_picks_sparse_for_sparse_inputs(bm, dg):
+    r_bits = 1 << 20
+    words = dg.bernoulli(dg.STREAM_TESTS + 11400, r_bits, np.array([1e-4] * 8 + [0.4] * 8))
+    flat, offs = dg.positions(words, r_bits)
+    with bm.Pool(r_bits, 16) as pool:
+        pool.put_dense(words)
+        pool.put_positions(flat, offs)
+        assert bm.query_select(pool, dg.Query(np.arange(8), 0, theta=2))[0] == bm.PATH_SPARSE
+        assert bm.query_select(pool, dg.Query(np.arange(8, 16), 0, theta=2))[0] == bm.PATH_DENSE
