@@ -156,6 +156,117 @@ def cpu_sample_time(words, queries, r_bits, budget_s: float):
     return nbytes / dt, nw, dt
 
 
+def bench_batched(bm, datagen, passes: int = 2):
+    """Mixed batch (2000 x 2^24 pool, 4096 queries): plain one query per
+    launch vs one batched graph replay; queries/s of each."""
+    import torch
+    r_bits = 1 << 24
+    words, _ = datagen.mixed_pool(2000, r_bits)
+    queries = datagen.mixed_queries(4096, 2000)
+    pool = bm.Pool(r_bits, 2000)
+    pool.put_dense(words)
+    del words
+    outs = [pool.empty_words() for _ in queries]
+    cards_plain = torch.zeros(len(queries), dtype=torch.int64, device="cuda")
+    cards_batch = torch.zeros(len(queries), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def plain():
+        for i, q in enumerate(queries):
+            bm.query_run(pool, q, outs[i], cards_plain[i:i + 1], path=bm.PATH_DENSE)
+
+    def batched():
+        bm.threshold_batch(pool, queries, outs, cards_batch, paths=[bm.PATH_DENSE] * len(queries))
+
+    def timed(fn):
+        fn()  # warm-up (graph capture on first use)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(passes):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return best
+
+    t_plain = timed(plain)
+    t_batch = timed(batched)
+    same = bool(torch.equal(cards_plain, cards_batch))
+    pool.status()
+    logical = sum(query_bytes(q.n, r_bits) for q in queries)
+    pool.close()
+    return {"workload": "mixed: 2000 x 2^24 pool (densities log-uniform [1e-4,0.5]), 4096 queries "
+                        "N log-uniform [3,1000], 10% intervals",
+            "plain_queries_per_s": round(len(queries) / t_plain, 1),
+            "batched_queries_per_s": round(len(queries) / t_batch, 1),
+            "speedup": round(t_plain / t_batch, 3),
+            "plain_logical_GBps": round(logical / t_plain / 1e9, 1),
+            "batched_logical_GBps": round(logical / t_batch / 1e9, 1),
+            "cardinalities_equal": same, "timing": f"best of {passes} passes, CUDA events"}
+
+
+def bench_selector(bm, datagen, n_train: int = 600):
+    """Sparse workload (5000 x 2^24, dense + lists; 2000 queries): train the
+    selector on its own timings of separate training queries, then report
+    time lost on the 2000 workload queries for the network and the fixed
+    rule, and queries/s of the batched+selected form vs plain dense."""
+    import torch
+    from paper_1402_4073_gb300 import selector
+    r_bits = 1 << 24
+    words, flat, offs, _ = datagen.sparse_pool(5000, r_bits)
+    test_q = datagen.sparse_queries(2000, 5000)
+    train_q = datagen.sparse_queries(n_train, 5000, stream=datagen.STREAM_SPARSE + (7 << 32))
+    pool = bm.Pool(r_bits, 5000)
+    pool.put_dense(words)
+    pool.put_positions(flat, offs)
+    del words, flat
+    ftr, ttr = selector.collect(pool, train_q, reps=3)
+    fte, tte = selector.collect(pool, test_q, reps=3)
+    t0 = time.perf_counter()
+    model = selector.train(ftr, ttr, steps=3000)
+    train_s = time.perf_counter() - t0
+    res = selector.evaluate(pool, model, test_q, fte, tte)
+    selector.install(pool, model)
+    outs = [pool.empty_words() for _ in test_q]
+    cards_a = torch.zeros(len(test_q), dtype=torch.int64, device="cuda")
+    cards_b = torch.zeros(len(test_q), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, passes=2):
+        fn()
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(passes):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return best
+
+    t_plain = timed(lambda: [bm.query_run(pool, q, outs[i], cards_a[i:i + 1], path=bm.PATH_DENSE)
+                             for i, q in enumerate(test_q)])
+    chosen = []
+    t_sel = timed(lambda: chosen.append(bm.threshold_batch(pool, test_q, outs, cards_b)))
+    same = bool(torch.equal(cards_a, cards_b))
+    pool.status()
+    pool.close()
+    out = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in res.items()}
+    out.update({"workload": "sparse: 5000 x 2^24 pool (densities log-uniform [1e-5,1e-2], dense + "
+                            "position lists), 2000 queries N log-uniform [2,4096], theta<=min(N,64)",
+                "train_queries": n_train, "train_steps": 3000, "train_s": round(train_s, 2),
+                "final_train_loss": round(model.final_loss, 5),
+                "plain_dense_queries_per_s": round(len(test_q) / t_plain, 1),
+                "batched_selected_queries_per_s": round(len(test_q) / t_sel, 1),
+                "speedup": round(t_plain / t_sel, 3),
+                "sparse_share": round(float((chosen[-1] == bm.PATH_SPARSE).mean()), 3),
+                "cardinalities_equal": same})
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_setup("gloo")
     if rank != 0:
@@ -206,7 +317,9 @@ def main():
     ap.add_argument("--r-log2", type=int, default=26,
                     help="rows = 2^r_log2 (smaller cases are for profiling only)")
     ap.add_argument("--dense-config", default="",
-                    help="variant,threads,stages,ctas_per_sm: skip the variant search")
+                    help="variant,threads,stages,ctas_per_sm[,adder]: skip the variant search")
+    ap.add_argument("--parts", default="dense,batch,selector",
+                    help="comma list of dense, batch, selector")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     global R_BITS, WORKLOAD
@@ -243,7 +356,8 @@ def main():
             bm.symmetric(pool, q.ids, tables[i], o, cards[i:i + 1])
 
     # pick the dense feeding variant by timing a few candidates (results are identical)
-    candidates = [(1, 128, 4, 1), (1, 128, 3, 1), (1, 64, 6, 2), (1, 64, 4, 3), (0, 256, 4, 2),
+    candidates = [(1, 128, 4, 1), (1, 128, 3, 1), (1, 64, 6, 2), (1, 64, 4, 3), (0, 256, 4, 2, 1),
+                  (0, 256, 4, 2),
                   (0, 256, 4, 3)]
     if args.dense_config:
         candidates = [tuple(int(x) for x in args.dense_config.split(","))]
@@ -336,6 +450,14 @@ def main():
                "sample": f"the 4 queries over the first {nw} of {words.shape[1]} words "
                          f"({64 * nw} rows), {dt:.1f} s"}
 
+    pool.close()
+    extra = {}
+    parts = args.parts.split(",")
+    if "batch" in parts:
+        extra["batched"] = bench_batched(bm, datagen)
+    if "selector" in parts:
+        extra["selector"] = bench_selector(bm, datagen)
+
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
@@ -357,8 +479,8 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": nq * args.steps,
             "clocks": clocks,
+            **extra,
         }))
-    pool.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
