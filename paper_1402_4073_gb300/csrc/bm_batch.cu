@@ -16,6 +16,7 @@
 #include <map>
 
 #include "bm_dense_common.cuh"
+#include "bm_scan_common.cuh"
 #include "bm_select.h"
 
 namespace bm {
@@ -115,9 +116,8 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 1)
     __shared__ unsigned long long item_s;
     __shared__ unsigned long long part[kSparseBatchThreads / 32];
     uint32_t* tab = sm;                      // up to 2048 words (n <= 65535)
-    uint32_t* cnt = sm + 2048;               // 16-bit counters, two per word
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t nwarps = blockDim.x >> 5;
+    uint32_t* scratch = sm + 2048;
+    uint32_t* cnt = scratch + ((kScanSmemWords + 3) & ~3u);  // 16-bit counters, two per word
     const uint32_t ns = h->n_sparse;
     const uint64_t total = ns ? h->sparse_off[ns] : 0;
     for (;;) {
@@ -167,29 +167,14 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 1)
         const uint32_t sub = tile_rows / kListTileRows;
         const uint64_t t0 = tile * sub;
         const uint64_t t1 = (t0 + sub < pa.tiles_per_list) ? t0 + sub : (uint64_t)pa.tiles_per_list;
-        for (uint32_t j = warp; j < n; j += nwarps) {
-            const uint32_t id = __ldg(d->ids + j);
-            const uint32_t* idx = pa.tile_index + (uint64_t)id * (pa.tiles_per_list + 1);
-            const uint32_t* pos = pa.positions + __ldg(pa.list_begin + id);
-            const uint32_t b = __ldg(idx + t0), e = __ldg(idx + t1);
-            for (uint32_t k = b + lane; k < e; k += 32) {
-                const uint32_t row = __ldg(pos + k) - (uint32_t)rlo;
-                atomicAdd(&cnt[row / 2], 1u << (16 * (row % 2)));
-            }
-        }
+        count_tile<16>(cnt, scratch, d->ids, n, pa.positions, pa.list_begin, pa.tile_index,
+                       pa.tiles_per_list, t0, t1, (uint32_t)rlo);
         __syncthreads();
         const uint32_t lanes = (uint32_t)((rhi - rlo + 31) / 32);
         uint32_t* out32 = reinterpret_cast<uint32_t*>(d->out);
         unsigned long long card = 0;
         for (uint32_t l = threadIdx.x; l < lanes; l += blockDim.x) {
-            uint32_t o = 0;
-#pragma unroll
-            for (uint32_t w = 0; w < 16; ++w) {
-                const uint32_t word = cnt[l * 16 + w];
-                const uint32_t c0 = word & 0xFFFFu, c1 = word >> 16;
-                o |= ((tab[c0 >> 5] >> (c0 & 31u)) & 1u) << (2 * w);
-                o |= ((tab[c1 >> 5] >> (c1 & 31u)) & 1u) << (2 * w + 1);
-            }
+            uint32_t o = counters_to_lane<16>(cnt + l * 16, pred, tab);
             const uint64_t row0 = rlo + 32ull * l;
             if (row0 + 32 > pa.r_bits) o &= (1u << (pa.r_bits - row0)) - 1u;
             out32[row0 / 32] = o;
@@ -203,7 +188,9 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 1)
     }
 }
 
-size_t sparse_batch_smem() { return (2048 + (size_t)kSparseMaxTile / 2) * 4; }
+size_t sparse_batch_smem() {
+    return (2048 + (((size_t)kScanSmemWords + 3) & ~(size_t)3) + (size_t)kSparseMaxTile / 2) * 4;
+}
 
 }  // namespace
 

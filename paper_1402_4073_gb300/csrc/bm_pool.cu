@@ -248,6 +248,8 @@ int bm_pool_put_positions(bm_pool* p, uint32_t first_id, uint32_t count, const u
         if (offsets[j + 1] < offsets[j]) return BM_EINVAL;
     if (total && !positions) return BM_EINVAL;
     if (total > 0xFFFFFFFFull) return BM_EINVAL;  // tile index entries are 32-bit
+    // kernels address the arena with 32-bit entry offsets
+    if (p->pos_used + total > 0xFFFFFFFFull) return BM_ENOMEM;
     std::lock_guard<std::mutex> lk(p->mu);
     BM_CUDA_TRY(cudaSetDevice(p->device));
     if (!on_device) {

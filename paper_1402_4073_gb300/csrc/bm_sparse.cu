@@ -5,14 +5,15 @@
 // GPU form: the rows are cut into tiles; a CTA owns one tile's counters in
 // shared memory (8-bit counters when n <= 255, else 16-bit: the paper's
 // width switch by N, packed four or two to a 32-bit word and incremented
-// with shared-memory atomics).  Each warp takes whole lists; the tile's slice
-// of a list comes from the pool's per-list tile index (first entry at every
-// multiple of 8192 rows), so a list is never searched.  Then each thread
+// with shared-memory atomics).  The tile's slice of a list comes from the
+// pool's per-list tile index (first entry at every multiple of 8192 rows), so
+// a list is never searched; the slices of up to 1024 lists are concatenated
+// and walked by all threads at once (bm_scan_common.cuh).  Then each thread
 // turns 32 counters into one 32-bit output lane through the truth table of f
 // held in shared memory, stores it and popcounts it.
 #include <algorithm>
 
-#include "bm_device.cuh"
+#include "bm_scan_common.cuh"
 
 namespace bm {
 namespace {
@@ -45,11 +46,12 @@ __global__ void __launch_bounds__(512) scancount_kernel(SparseArgs a) {
     constexpr uint32_t kPer = 32 / BITS;  // counters per 32-bit word
     const uint32_t tab_words = (a.n + 1 + 31) / 32;
     uint32_t* tab = sm;
-    uint32_t* cnt = sm + ((tab_words + 3) & ~3u);
+    uint32_t* scratch = sm + ((tab_words + 3) & ~3u);
+    uint32_t* cnt = scratch + ((kScanSmemWords + 3) & ~3u);
     const uint32_t cnt_words = a.tile_rows / kPer;
     build_truth(a.pred, a.n, tab, tab_words);
 
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const uint32_t lane = threadIdx.x & 31;
     const uint64_t ntiles = (a.r_bits + a.tile_rows - 1) / a.tile_rows;
     const uint32_t sub = a.tile_rows / kListTileRows;  // index entries per tile
     unsigned long long card = 0;
@@ -60,31 +62,14 @@ __global__ void __launch_bounds__(512) scancount_kernel(SparseArgs a) {
         __syncthreads();
         const uint64_t t0 = tile * sub;
         const uint64_t t1 = (t0 + sub < a.tiles_per_list) ? t0 + sub : (uint64_t)a.tiles_per_list;
-        for (uint32_t j = warp; j < a.n; j += nwarps) {
-            const uint32_t id = __ldg(a.ids + j);
-            const uint32_t* idx = a.tile_index + (uint64_t)id * (a.tiles_per_list + 1);
-            const uint32_t* pos = a.positions + __ldg(a.list_begin + id);
-            const uint32_t b = __ldg(idx + t0), e = __ldg(idx + t1);
-            for (uint32_t k = b + lane; k < e; k += 32) {
-                const uint32_t row = __ldg(pos + k) - (uint32_t)lo;
-                atomicAdd(&cnt[row / kPer], 1u << (BITS * (row % kPer)));
-            }
-        }
+        count_tile<BITS>(cnt, scratch, a.ids, a.n, a.positions, a.list_begin, a.tile_index,
+                         a.tiles_per_list, t0, t1, (uint32_t)lo);
         __syncthreads();
         // 32 rows per thread -> one 32-bit output lane
         const uint32_t lanes = (uint32_t)((hi - lo + 31) / 32);
         uint32_t* out32 = reinterpret_cast<uint32_t*>(a.out);
         for (uint32_t l = threadIdx.x; l < lanes; l += blockDim.x) {
-            uint32_t o = 0;
-#pragma unroll
-            for (uint32_t w = 0; w < 32 / kPer; ++w) {
-                const uint32_t word = cnt[l * (32 / kPer) + w];
-#pragma unroll
-                for (uint32_t s = 0; s < kPer; ++s) {
-                    const uint32_t c = (word >> (BITS * s)) & ((1u << BITS) - 1u);
-                    o |= ((tab[c >> 5] >> (c & 31u)) & 1u) << (w * kPer + s);
-                }
-            }
+            uint32_t o = counters_to_lane<BITS>(cnt + l * (32 / kPer), a.pred, tab);
             const uint64_t row0 = lo + 32ull * l;
             if (row0 + 32 > a.r_bits) o &= (1u << (a.r_bits - row0)) - 1u;  // rows >= r
             out32[row0 / 32] = o;
@@ -107,7 +92,8 @@ int launch_sparse(const SparseArgs& a, const SparseConfig& cfg, int sm_count, cu
     if (a.tile_rows == 0 || a.tile_rows % kListTileRows) return BM_EINVAL;
     const int bits = a.n <= 255 ? 8 : 16;
     const size_t tab_words = ((size_t)(a.n + 1 + 31) / 32 + 3) & ~(size_t)3;
-    const size_t smem = (tab_words + (size_t)a.tile_rows * bits / 32) * 4;
+    const size_t scratch_words = ((size_t)dev::kScanSmemWords + 3) & ~(size_t)3;
+    const size_t smem = (tab_words + scratch_words + (size_t)a.tile_rows * bits / 32) * 4;
     const uint64_t ntiles = (a.r_bits + a.tile_rows - 1) / a.tile_rows;
     const int threads = std::max(64, std::min(512, cfg.threads));
     const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);
