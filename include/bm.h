@@ -242,6 +242,90 @@ int bm_pool_set_batch_config(bm_pool* pool, int ctas_per_sm, int adder);
  */
 int bm_cardinality(const uint64_t* words, uint64_t r_bits, uint64_t* out_card, void* stream);
 
+/*
+ * Failure-path self-test: launch a one-warp kernel that waits on a device
+ * barrier phase nothing completes, with a bound of limit_us microseconds
+ * (1 .. 2,000,000).  The wait expires, the kernel sets the pool's error word
+ * and returns; the next bm_pool_status() reports BM_ETIMEOUT.  The GPU
+ * context stays usable.  Every bounded wait of the library reports this way.
+ */
+int bm_pool_selftest_wait(bm_pool* pool, uint32_t limit_us, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Serving loop (not in the paper): continuous batching over a resident pool
+ * ---------------------------------------------------------------------- */
+
+typedef struct bm_server bm_server;
+
+typedef struct bm_server_config {
+    uint64_t mem_budget;      /* device bytes for result bitmaps of admitted requests */
+    uint32_t max_batch;       /* most requests per batch launch */
+    uint32_t max_inflight;    /* batches in flight at once, on as many streams (1..4) */
+    uint32_t max_queue;       /* most requests waiting for admission; more: BM_EBUSY */
+    uint32_t batch_window_us; /* pause before forming a batch, to let it grow (0: none) */
+} bm_server_config;
+
+typedef struct bm_server_stats_t {
+    uint64_t submitted, completed, refused, batches, batched_queries;
+    uint32_t waiting;         /* requests not yet admitted */
+    uint32_t free_slots, total_slots;
+    uint32_t max_batch_seen;
+    int32_t last_error;       /* last launch error (BM_OK if none) */
+} bm_server_stats_t;
+
+/*
+ * Start a serving loop over `pool`: a scheduler thread forms batches of
+ * waiting requests whenever one of max_inflight streams is free and runs
+ * each with bm_threshold_batch.  Admission is by device memory: the server
+ * allocates mem_budget bytes once and a request is admitted only when an
+ * output slot (one bitmap, ceil(r/64) words rounded to 256 bytes) is free;
+ * slots come back when results are released.  BM_ENOMEM if the budget holds
+ * no slot or cannot be allocated.
+ */
+int bm_server_create(bm_pool* pool, const bm_server_config* cfg, bm_server** out);
+
+/* Stop the scheduler, wait for batches in flight, free everything. */
+int bm_server_destroy(bm_server* server);
+
+/*
+ * Submit a query (its out_words is ignored: the result lives in a server
+ * slot).  The query is copied; ids are validated at once (BM_EINVAL,
+ * BM_ERANGE).  BM_EBUSY when max_queue requests already wait.  *ticket
+ * identifies the request.
+ */
+int bm_server_submit(bm_server* server, const bm_query* q, uint64_t* ticket);
+
+/* Wait up to timeout_ms for a request: BM_OK, BM_ETIMEOUT, or its launch error. */
+int bm_server_wait(bm_server* server, uint64_t ticket, uint32_t timeout_ms);
+
+/*
+ * Result of a completed request: the output bitmap copied to host_words
+ * (ceil(r/64) words; may be NULL), its cardinality, the latency from submit
+ * to batch completion and the part spent waiting before launch (both in
+ * microseconds), and the path it ran on.  BM_ENOTREADY if not complete.
+ * Any output pointer may be NULL.
+ */
+int bm_server_result(bm_server* server, uint64_t ticket, uint64_t* host_words, uint64_t* card,
+                     double* latency_us, double* queue_us, int32_t* path);
+
+/* Forget a completed request and return its output slot. */
+int bm_server_release(bm_server* server, uint64_t ticket);
+
+/*
+ * Load generator for the serving loop: submit qs[i] at arrival_s[i] seconds
+ * after the call starts (open loop, e.g. Poisson arrivals), collect every
+ * result in order and release it.  Per request (host arrays of n entries,
+ * each may be NULL): latency_us and queue_us as in bm_server_result, cards,
+ * and status (BM_OK, BM_EBUSY when refused by admission, or an error).
+ * *wall_s: time from the first submission to the last collection.
+ */
+int bm_server_replay(bm_server* server, const bm_query* qs, uint32_t n, const double* arrival_s,
+                     double* latency_us, double* queue_us, uint64_t* cards, int32_t* status,
+                     double* wall_s);
+
+/* Counters of the serving loop. */
+int bm_server_stats(bm_server* server, bm_server_stats_t* out);
+
 /* ------------------------------------------------------------------------
  * Learned kernel selector (not in the paper: the paper compares its
  * algorithms by measured time per query and reports each one's

@@ -28,6 +28,17 @@ class bm_pool_info_t(ctypes.Structure):
                 ("device_bytes", u64), ("dense_base", vp)]
 
 
+class bm_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget", u64), ("max_batch", u32), ("max_inflight", u32), ("max_queue", u32),
+                ("batch_window_us", u32)]
+
+
+class bm_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", u64), ("completed", u64), ("refused", u64), ("batches", u64),
+                ("batched_queries", u64), ("waiting", u32), ("free_slots", u32),
+                ("total_slots", u32), ("max_batch_seen", u32), ("last_error", ctypes.c_int32)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "bm_strerror": (ctypes.c_char_p, [i32]),
@@ -53,6 +64,15 @@ SIGNATURES = {
     "bm_mlp_backward": (i32, [vp, u32, u32, u32, vp, vp, vp, vp, vp, u32, vp, vp, vp, vp]),
     "bm_mlp_adam": (i32, [vp, vp, vp, vp, u64, u32, ctypes.c_float, ctypes.c_float,
                           ctypes.c_float, ctypes.c_float, vp]),
+    "bm_pool_selftest_wait": (i32, [vp, u32, vp]),
+    "bm_server_create": (i32, [vp, ctypes.POINTER(bm_server_config), ctypes.POINTER(vp)]),
+    "bm_server_destroy": (i32, [vp]),
+    "bm_server_submit": (i32, [vp, vp, ctypes.POINTER(u64)]),
+    "bm_server_wait": (i32, [vp, u64, u32]),
+    "bm_server_result": (i32, [vp, u64, vp, vp, vp, vp, vp]),
+    "bm_server_release": (i32, [vp, u64]),
+    "bm_server_stats": (i32, [vp, ctypes.POINTER(bm_server_stats_t)]),
+    "bm_server_replay": (i32, [vp, vp, u32, vp, vp, vp, vp, vp, vp]),
     "bm_threshold_noalloc": (i32, [vp, u64, u32, u64, vp, u32, u32, vp, vp, vp]),
 }
 

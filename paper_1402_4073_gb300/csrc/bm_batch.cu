@@ -206,7 +206,7 @@ struct BatchSlot {
 };
 
 struct BatchState {
-    static constexpr int kSlots = 3;
+    static constexpr int kSlots = 4;
     BatchSlot slots[kSlots];
     int next = 0;
     cudaStream_t capture = nullptr;

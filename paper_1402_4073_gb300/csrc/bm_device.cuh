@@ -191,12 +191,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Wait for the phase of parity `parity` to complete; give up after
 // kWaitLimitNs, set the error word and return false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (uint32_t spin = 1;; ++spin) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((spin & 63u) == 0 && globaltimer() - t0 > kWaitLimitNs) {
+        if ((spin & 63u) == 0 && globaltimer() - t0 > limit_ns) {
             if (err) atomicOr(err, kErrTimeout);
             return false;
         }

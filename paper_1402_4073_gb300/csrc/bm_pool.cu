@@ -123,6 +123,17 @@ __global__ void list_index_kernel(const uint32_t* pos, uint64_t len, uint32_t ti
     idx[t] = (uint32_t)lo;
 }
 
+// Self-test of the bounded-wait path: wait on an mbarrier phase that nothing
+// completes; the wait gives up after limit_ns and sets the error word.
+__global__ void wait_selftest_kernel(int* err, unsigned long long limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        dev::mbar_init(&bar, 1);
+        dev::fence_barrier_init();
+        dev::mbar_wait_bounded(&bar, 0, err, limit_ns);  // no thread arrives: expires
+    }
+}
+
 // Strict increase and range check of device-resident lists; sets *bad.
 __global__ void list_check_kernel(const uint32_t* pos, uint64_t len, uint64_t r_bits, int* bad) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
@@ -366,6 +377,16 @@ int bm_pool_status(bm_pool* p) {
         BM_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
         return BM_ETIMEOUT;
     }
+    return BM_OK;
+}
+
+int bm_pool_selftest_wait(bm_pool* p, uint32_t limit_us, void* stream) {
+    if (!p || limit_us == 0 || limit_us > 2000000) return BM_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    BM_CUDA_TRY(cudaSetDevice(p->device));
+    wait_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(
+        p->d_err, (unsigned long long)limit_us * 1000ull);
+    BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
 }
 

@@ -1,0 +1,133 @@
+"""Serving loop: each result is the same alone and in the mix (bit-exact),
+admission waits for device memory, a full queue refuses, bad requests are
+rejected at submission, and batches form under load."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bm():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1402_4073_gb300 as bm
+    return bm
+
+
+@pytest.fixture(scope="module")
+def served(bm, dg):
+    """Scaled serving workload: 400 bitmaps of r = 2^18 + 5 rows, densities
+    log-uniform in [1e-5, 0.5], lists for every bitmap; 120 queries with N
+    log-uniform in [2, 400] and Poisson arrivals at 20k queries/s."""
+    r_bits = (1 << 18) + 5
+    d = dg.pool_densities(dg.STREAM_TESTS + 15000, 400, 1e-5, 0.5)
+    words = dg.bernoulli(dg.STREAM_TESTS + 15001, r_bits, d)
+    flat, offs = dg.positions(words, r_bits)
+    queries = dg.serving_queries(120, 20000.0, pool=400, nmax=400,
+                                 stream=dg.STREAM_TESTS + 15002)
+    pool = bm.Pool(r_bits, 400)
+    pool.put_dense(words)
+    pool.put_positions(flat, offs)
+    yield pool, words, queries, r_bits
+    pool.close()
+
+
+def _slots(pool, n):
+    """Device bytes of n result slots (one bitmap rounded up to 256 bytes)."""
+    return n * ((pool.words * 8 + 255) // 256 * 256)
+
+
+def _alone(bm, pool, q):
+    o = pool.empty_words()
+    c = torch.zeros(1, dtype=torch.int64, device="cuda")
+    bm.query_run(pool, q, o, c)
+    torch.cuda.synchronize()
+    return bm.to_numpy_words(o), int(c.item())
+
+
+def test_results_same_alone_and_in_mix(bm, oracle_lib, served):
+    from paper_1402_4073_gb300.serve import Server
+    pool, words, queries, r_bits = served
+    with Server(pool, mem_budget=_slots(pool, 64), max_batch=32, max_inflight=2) as srv:
+        tickets = [srv.submit(q) for q in queries]  # a burst: forms batches
+        for q, t in zip(queries, tickets):
+            assert srv.wait(t, 20000) == 0
+            got_words, got_card, lat, qu, path = srv.result(t)
+            srv.release(t)
+            alone = _alone(bm, pool, q)
+            want = oracle_lib.query(words, q, r_bits)
+            assert np.array_equal(got_words, alone[0]) and got_card == alone[1]
+            assert np.array_equal(got_words, want[0]) and got_card == want[1]
+            assert lat >= qu >= 0
+        st = srv.stats()
+        assert st["completed"] == len(queries) and st["free_slots"] == st["total_slots"]
+        assert st["max_batch_seen"] > 1  # requests that waited together ran together
+
+
+def test_poisson_replay_cards_match(bm, oracle_lib, served):
+    from paper_1402_4073_gb300.serve import Server, summarize
+    pool, words, queries, r_bits = served
+    with Server(pool, mem_budget=_slots(pool, 256), max_batch=64, max_inflight=2) as srv:
+        res = srv.replay(queries, [q.arrival_s for q in queries])
+        s = summarize(res, 20000.0)
+        assert s["completed"] == len(queries) and s["errors"] == 0
+        for i, q in enumerate(queries):
+            assert int(res["cards"][i]) == oracle_lib.query(words, q, r_bits)[1]
+        assert s["p99_us"] >= s["p50_us"] > 0
+
+
+def test_admission_waits_for_memory(bm, served):
+    from paper_1402_4073_gb300.serve import Server
+    pool, words, queries, r_bits = served
+    with Server(pool, mem_budget=_slots(pool, 3) + 255, max_batch=8, max_inflight=1) as srv:
+        assert srv.stats()["total_slots"] == 3
+        tickets = [srv.submit(q) for q in queries[:8]]
+        for t in tickets[:3]:
+            assert srv.wait(t, 20000) == 0
+        # no slot is free until a result is released: the rest wait
+        assert srv.wait(tickets[3], 300) == bm.BM_ETIMEOUT
+        st = srv.stats()
+        assert st["free_slots"] == 0 and st["waiting"] == 5
+        srv.release(tickets[0])
+        assert srv.wait(tickets[3], 20000) == 0
+        for t in tickets[1:4]:
+            srv.release(t)
+        for t in tickets[4:]:
+            assert srv.wait(t, 20000) == 0
+            srv.release(t)
+        assert srv.stats()["free_slots"] == 3
+
+
+def test_queue_limit_and_bad_requests(bm, dg, served):
+    from paper_1402_4073_gb300.serve import Server
+    pool, words, queries, r_bits = served
+    with Server(pool, mem_budget=_slots(pool, 1), max_batch=4, max_inflight=1, max_queue=2) as srv:
+        first = srv.submit(queries[0])
+        assert srv.wait(first, 20000) == 0  # holds the only slot
+        srv.submit(queries[1])
+        srv.submit(queries[2])
+        with pytest.raises(bm.BMError) as e:
+            srv.submit(queries[3])
+        assert e.value.code == bm.BM_EBUSY
+        assert srv.stats()["refused"] == 1
+        with pytest.raises(bm.BMError) as e:
+            srv.submit(dg.Query(np.array([0, 400]), 0, theta=1))
+        assert e.value.code == bm.BM_ERANGE
+        srv.release(first)
+
+
+def test_wait_timeout_self_test(bm, served):
+    """A device wait that nothing completes expires after its bound, the
+    error is reported on the host, and the context stays usable."""
+    pool, words, queries, r_bits = served
+    pool.status()
+    assert bm.lib.bm_pool_selftest_wait(pool.handle, 20000, None) == 0
+    with pytest.raises(bm.BMError) as e:
+        pool.status()
+    assert e.value.code == bm.BM_ETIMEOUT
+    pool.status()  # cleared
+    o, c = _alone(bm, pool, queries[0])
+    assert c >= 0
