@@ -267,6 +267,39 @@ def bench_selector(bm, datagen, n_train: int = 600):
     return out
 
 
+def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds: float = 0.8):
+    """Serving loop on the 10,000 x 2^22 pool: Poisson arrivals at each
+    offered rate; p50/p99 latency and achieved queries/s."""
+    from paper_1402_4073_gb300.serve import Server, summarize
+    r_bits = 1 << 22
+    words, _ = datagen.serving_pool(10000, r_bits)
+    pool = bm.Pool(r_bits, 10000)
+    pool.put_dense(words)
+    del words
+    out = []
+    slot = (pool.words * 8 + 255) // 256 * 256
+    with Server(pool, mem_budget=4096 * slot, max_batch=512, max_inflight=2) as srv:
+        # warm-up: graph capture and caches
+        warm = datagen.serving_queries(256, 50000.0, stream=datagen.STREAM_SERVING + (9 << 32))
+        srv.replay(warm, [q.arrival_s for q in warm])
+        for k, rate in enumerate(rates):
+            n = int(min(40000, max(500, rate * seconds)))
+            qs = datagen.serving_queries(n, float(rate),
+                                         stream=datagen.STREAM_SERVING + ((10 + k) << 32))
+            res = srv.replay(qs, [q.arrival_s for q in qs])
+            summ = summarize(res, float(rate))
+            summ["requests"] = n
+            out.append(summ)
+        st = srv.stats()
+    pool.status()
+    pool.close()
+    return {"workload": "serving: 10000 x 2^22 pool (densities log-uniform [1e-5,0.5]), Poisson "
+                        "arrivals, N log-uniform [2,4096], theta uniform [1,N]",
+            "admission": "4096 result slots (2 GiB); max batch 512; 2 batches in flight",
+            "mean_batch": round(st["batched_queries"] / max(1, st["batches"]), 1),
+            "rates": out}
+
+
 def run_reference(args):
     rank, world, _ = dist_setup("gloo")
     if rank != 0:
@@ -318,8 +351,8 @@ def main():
                     help="rows = 2^r_log2 (smaller cases are for profiling only)")
     ap.add_argument("--dense-config", default="",
                     help="variant,threads,stages,ctas_per_sm[,adder]: skip the variant search")
-    ap.add_argument("--parts", default="dense,batch,selector",
-                    help="comma list of dense, batch, selector")
+    ap.add_argument("--parts", default="dense,batch,selector,serving",
+                    help="comma list of dense, batch, selector, serving")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     global R_BITS, WORKLOAD
@@ -457,6 +490,8 @@ def main():
         extra["batched"] = bench_batched(bm, datagen)
     if "selector" in parts:
         extra["selector"] = bench_selector(bm, datagen)
+    if "serving" in parts:
+        extra["serving"] = bench_serving(bm, datagen)
 
     if rank == 0:
         print(json.dumps({

@@ -46,6 +46,7 @@ struct Batch {
     uint64_t* d_cards = nullptr;
     uint64_t* h_cards = nullptr;  // pinned
     std::vector<Request*> reqs;
+    std::vector<int32_t> paths;  // path each request ran on, filled before the callback
     bool busy = false;
     struct bm_server* srv = nullptr;
 };
@@ -86,6 +87,7 @@ void CUDART_CB on_batch_done(void* arg) {
         for (size_t i = 0; i < b->reqs.size(); ++i) {
             Request* r = b->reqs[i];
             r->card = b->h_cards[i];
+            r->path = b->paths[i];
             r->t_done = now;
             r->done = true;
         }
@@ -97,32 +99,19 @@ void CUDART_CB on_batch_done(void* arg) {
     s->cv_sched.notify_all();
 }
 
-// Launch one batch of admitted requests on a free stream (lock held).
-int launch_batch(bm_server* s, Batch& b, std::vector<Request*>& take) {
-    std::vector<bm_query> qs(take.size());
-    for (size_t i = 0; i < take.size(); ++i) qs[i] = take[i]->q;
-    std::vector<int32_t> paths(take.size());
-    const auto now = Clock::now();
-    int rc = bm_threshold_batch(s->pool, qs.data(), (uint32_t)qs.size(), b.d_cards, paths.data(),
+// Launch one batch of admitted requests on stream b.stream.  Called without
+// the server lock: CUDA calls inside (allocation, frees) may wait for the
+// device, and the device may be waiting for a host callback that needs the
+// lock.
+int launch_batch(bm_server* s, Batch& b, const std::vector<bm_query>& qs) {
+    b.paths.assign(qs.size(), 0);
+    int rc = bm_threshold_batch(s->pool, qs.data(), (uint32_t)qs.size(), b.d_cards, b.paths.data(),
                                 b.stream);
     if (rc) return rc;
-    if (cudaMemcpyAsync(b.h_cards, b.d_cards, 8 * take.size(), cudaMemcpyDeviceToHost, b.stream) !=
+    if (cudaMemcpyAsync(b.h_cards, b.d_cards, 8 * qs.size(), cudaMemcpyDeviceToHost, b.stream) !=
         cudaSuccess)
         return BM_ECUDA;
-    for (size_t i = 0; i < take.size(); ++i) {
-        take[i]->t_launch = now;
-        take[i]->path = paths[i];
-    }
-    b.reqs = take;
-    b.busy = true;
-    if (cudaLaunchHostFunc(b.stream, on_batch_done, &b) != cudaSuccess) {
-        b.reqs.clear();
-        b.busy = false;
-        return BM_ECUDA;
-    }
-    s->batches_run += 1;
-    s->batched_queries += take.size();
-    s->max_batch_seen = std::max<uint32_t>(s->max_batch_seen, (uint32_t)take.size());
+    if (cudaLaunchHostFunc(b.stream, on_batch_done, &b) != cudaSuccess) return BM_ECUDA;
     return BM_OK;
 }
 
@@ -154,21 +143,42 @@ void scheduler(bm_server* s) {
                 s->waiting.pop_front();
                 r->slot = s->free_slots.back();
                 s->free_slots.pop_back();
-                r->q.out_words = reinterpret_cast<uint64_t*>(s->d_arena + (uint64_t)r->slot * s->slot_bytes);
+                r->q.out_words =
+                    reinterpret_cast<uint64_t*>(s->d_arena + (uint64_t)r->slot * s->slot_bytes);
                 take.push_back(r);
             }
-            int rc = launch_batch(s, b, take);
+            b.reqs = take;
+            b.busy = true;
+            const auto now = Clock::now();
+            std::vector<bm_query> qs(take.size());
+            for (size_t i = 0; i < take.size(); ++i) {
+                take[i]->t_launch = now;
+                qs[i] = take[i]->q;
+            }
+            // Once the lock is dropped the batch may complete and its requests be
+            // collected and freed, so they are not touched again on success.
+            const size_t nb = take.size();
+            lk.unlock();
+            int rc = launch_batch(s, b, qs);
+            lk.lock();
             if (rc) {
                 // the batch could not run: its requests complete with the error
                 s->last_error = rc;
-                const auto now = Clock::now();
+                const auto t = Clock::now();
                 for (Request* r : take) {
                     r->done = true;
-                    r->t_launch = r->t_done = now;
+                    r->t_done = t;
                     r->path = rc;
                 }
+                b.reqs.clear();
+                b.busy = false;
                 s->cv_done.notify_all();
+            } else {
+                s->batches_run += 1;
+                s->batched_queries += nb;
+                s->max_batch_seen = std::max<uint32_t>(s->max_batch_seen, (uint32_t)nb);
             }
+            if (s->stop) break;
         }
     }
 }
@@ -337,16 +347,18 @@ int bm_server_replay(bm_server* s, const bm_query* qs, uint32_t n, const double*
     std::atomic<bool> submit_done{false};
     // collector: results in submission order, each slot released at once
     std::thread collector([&] {
+        bool stalled = false;
         for (uint32_t i = 0; i < n; ++i) {
             while (submitted.load() <= i && !submit_done.load())
                 std::this_thread::sleep_for(std::chrono::microseconds(20));
             if (i >= submitted.load()) break;
             if (st[i] != BM_OK) continue;
-            int rc = BM_ETIMEOUT;
-            for (int tries = 0; tries < 600 && rc == BM_ETIMEOUT; ++tries)  // at most 60 s
-                rc = bm_server_wait(s, tickets[i], 100);
+            // a request gets at most 10 s; after one expires the rest get 100 ms each
+            int rc = bm_server_wait(s, tickets[i], stalled ? 100 : 10000);
             if (rc != BM_OK) {
+                if (rc == BM_ETIMEOUT) stalled = true;
                 st[i] = rc;
+                if (rc != BM_ETIMEOUT) bm_server_release(s, tickets[i]);
                 continue;
             }
             double lat = 0, qu = 0;
