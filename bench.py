@@ -388,28 +388,14 @@ def main():
         else:
             bm.symmetric(pool, q.ids, tables[i], o, cards[i:i + 1])
 
-    # pick the dense feeding variant by timing a few candidates (results are identical)
-    candidates = [(1, 128, 4, 1), (1, 128, 3, 1), (1, 64, 6, 2), (1, 64, 4, 3), (0, 256, 4, 2, 1),
-                  (0, 256, 4, 2),
-                  (0, 256, 4, 3)]
+    # kernel shape: the library's autotuner (results are identical for every shape)
     if args.dense_config:
-        candidates = [tuple(int(x) for x in args.dense_config.split(","))]
-    best, best_t = None, 1e30
-    for c in candidates:
-        pool.set_dense_config(*c)
-        for _ in range(2):
-            launch(0, queries[0])
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(5):
-            launch(0, queries[0])
-        e1.record()
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1)
-        if t < best_t:
-            best, best_t = c, t
-        print(f"dense config {c}: {t / 5 * 1e3:.1f} us per query", file=sys.stderr)
-    pool.set_dense_config(*best)
+        pool.set_dense_config(*[int(x) for x in args.dense_config.split(",")])
+        tune_report = "fixed by --dense-config"
+    else:
+        tune_report = pool.autotune()
+        print(f"autotune: {tune_report}", file=sys.stderr)
+    best = pool.configs()["dense"]
     pool.status()
 
     for _ in range(args.warmup):
@@ -502,7 +488,7 @@ def main():
             "config": {"workload": WORKLOAD, "N": N, "r_bits": R_BITS, "queries_per_step": nq,
                        "queries_per_s": round(nq * args.steps * world / (el_ms / 1e3), 1),
                        "l2": "inputs (2.15 GB per query) larger than L2; no flush",
-                       "dense_config": list(best)},
+                       "dense_config": best, "autotune": tune_report},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "peak_source": f"hbm_gbs of {peak_src}",

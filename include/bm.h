@@ -131,28 +131,59 @@ int bm_pool_bitmap_cardinality(const bm_pool* pool, uint32_t id, uint64_t* out);
 int bm_pool_status(bm_pool* pool);
 
 /*
- * Choose how the pool's dense kernel feeds its inputs (the autotuner sets
- * this; results are identical for every choice).
- *   variant 0: direct 128-bit streaming loads; `threads` ignored (256).
+ * Shape of the pool's dense kernel (results are identical for every choice;
+ * bm_pool_autotune picks one by measurement).
+ *   variant 0: direct streaming loads, 256 threads per CTA; `threads` and
+ *              `stages` ignored.
  *   variant 1: bulk-copy (TMA) pipeline through shared memory with
  *              `threads` consumer threads per CTA (64 or 128) and `stages`
  *              pipeline stages (2..8) of 16 bitmaps each.
  * ctas_per_sm (1..8) caps the persistent grid at ctas_per_sm x SM count.
  * adder: layout of the adder tree (Sec. 4.3 "Sideways Sum"): 0 = blocks of
- * 16 inputs through 15 full adders, 1 = blocks of 8 inputs through 7 (fewer
- * live registers, one more carry ripple per 8 inputs); variant 0 only.
+ *   16 inputs through 15 full adders, 1 = blocks of 8 inputs through 7
+ *   (fewer live registers, one more carry ripple per 8 inputs); variant 0.
+ * words_per_thread: 64-bit words of each input a thread owns, 2 (16-byte
+ *   loads) or 1 (8-byte loads, twice the threads per row range); variant 0.
  * BM_EINVAL for values outside these ranges.
  */
-int bm_pool_set_dense_config(bm_pool* pool, int variant, int threads, int stages,
-                             int ctas_per_sm, int adder);
+typedef struct bm_dense_config_t {
+    int32_t variant, threads, stages, ctas_per_sm, adder, words_per_thread;
+} bm_dense_config_t;
+int bm_pool_set_dense_config(bm_pool* pool, const bm_dense_config_t* cfg);
+int bm_pool_get_dense_config(bm_pool* pool, bm_dense_config_t* cfg);
 
 /*
- * Choose the sparse (ScanCount) kernel's shape: tile_rows rows of counters
- * per CTA (a multiple of 8192, at most 65536 with 16-bit counters),
- * `threads` per CTA (64..512, a multiple of 32), ctas_per_sm (1..8).
- * BM_EINVAL outside these ranges.
+ * Shape of the sparse (ScanCount) kernel: tile_rows rows of counters per CTA
+ * (a multiple of 8192, at most 65536), `threads` per CTA (64..512, a
+ * multiple of 32), ctas_per_sm (1..8).  BM_EINVAL outside these ranges.
  */
-int bm_pool_set_sparse_config(bm_pool* pool, uint32_t tile_rows, int threads, int ctas_per_sm);
+typedef struct bm_sparse_config_t {
+    uint32_t tile_rows;
+    int32_t threads, ctas_per_sm;
+} bm_sparse_config_t;
+int bm_pool_set_sparse_config(bm_pool* pool, const bm_sparse_config_t* cfg);
+int bm_pool_get_sparse_config(bm_pool* pool, bm_sparse_config_t* cfg);
+
+/*
+ * Shape of the batch kernel: dense persistent CTAs per SM (1 or 2), adder
+ * layout and words per thread (as for the dense kernel).
+ */
+typedef struct bm_batch_config_t {
+    int32_t ctas_per_sm, adder, words_per_thread;
+} bm_batch_config_t;
+int bm_pool_set_batch_config(bm_pool* pool, const bm_batch_config_t* cfg);
+int bm_pool_get_batch_config(bm_pool* pool, bm_batch_config_t* cfg);
+
+/*
+ * Autotuner: time candidate shapes of the dense, sparse (if lists are
+ * loaded) and batch kernels on queries over the pool's own bitmaps (CUDA
+ * events, median of repeats) and install the fastest of each.  With a
+ * cache_path, a result stored there for the same GPU model and pool shape
+ * is reused instead of measuring, and new results are appended.  report
+ * (may be NULL) receives a one-line text summary, truncated to report_len.
+ * Needs at least one loaded dense bitmap.  Synchronous.
+ */
+int bm_pool_autotune(bm_pool* pool, const char* cache_path, char* report, uint64_t report_len);
 
 /* ------------------------------------------------------------------------
  * Single queries
@@ -228,12 +259,6 @@ int bm_query_run(bm_pool* pool, const bm_query* q, uint64_t* out_card, int32_t* 
  */
 int bm_threshold_batch(bm_pool* pool, const bm_query* q, uint32_t nq, uint64_t* out_cards,
                        int32_t* chosen_paths, void* stream);
-
-/*
- * Batch kernel shape: dense persistent CTAs per SM (1 or 2) and adder layout
- * (as in bm_pool_set_dense_config).  Results are identical for every choice.
- */
-int bm_pool_set_batch_config(bm_pool* pool, int ctas_per_sm, int adder);
 
 /*
  * Number of ones among the first r_bits rows of a device bitmap `words`

@@ -142,18 +142,35 @@ class Pool:
         check(lib.bm_pool_status(self.handle), "bm_pool_status")
 
     def set_dense_config(self, variant: int, threads: int = 128, stages: int = 4,
-                         ctas_per_sm: int = 1, adder: int = 0) -> None:
-        check(lib.bm_pool_set_dense_config(self.handle, variant, threads, stages, ctas_per_sm,
-                                           adder), "bm_pool_set_dense_config")
+                         ctas_per_sm: int = 1, adder: int = 0, words_per_thread: int = 2) -> None:
+        c = _native.bm_dense_config_t(variant, threads, stages, ctas_per_sm, adder, words_per_thread)
+        check(lib.bm_pool_set_dense_config(self.handle, ctypes.byref(c)), "bm_pool_set_dense_config")
 
     def set_sparse_config(self, tile_rows: int = 32768, threads: int = 512,
                           ctas_per_sm: int = 2) -> None:
-        check(lib.bm_pool_set_sparse_config(self.handle, tile_rows, threads, ctas_per_sm),
+        c = _native.bm_sparse_config_t(tile_rows, threads, ctas_per_sm)
+        check(lib.bm_pool_set_sparse_config(self.handle, ctypes.byref(c)),
               "bm_pool_set_sparse_config")
 
-    def set_batch_config(self, ctas_per_sm: int = 2, adder: int = 0) -> None:
-        check(lib.bm_pool_set_batch_config(self.handle, ctas_per_sm, adder),
-              "bm_pool_set_batch_config")
+    def set_batch_config(self, ctas_per_sm: int = 2, adder: int = 0,
+                         words_per_thread: int = 2) -> None:
+        c = _native.bm_batch_config_t(ctas_per_sm, adder, words_per_thread)
+        check(lib.bm_pool_set_batch_config(self.handle, ctypes.byref(c)), "bm_pool_set_batch_config")
+
+    def configs(self) -> dict:
+        d, s, b = _native.bm_dense_config_t(), _native.bm_sparse_config_t(), _native.bm_batch_config_t()
+        check(lib.bm_pool_get_dense_config(self.handle, ctypes.byref(d)))
+        check(lib.bm_pool_get_sparse_config(self.handle, ctypes.byref(s)))
+        check(lib.bm_pool_get_batch_config(self.handle, ctypes.byref(b)))
+        as_dict = lambda x: {k: getattr(x, k) for k, _ in x._fields_}
+        return {"dense": as_dict(d), "sparse": as_dict(s), "batch": as_dict(b)}
+
+    def autotune(self, cache_path: str | None = None) -> str:
+        """Measure kernel shapes on this pool and install the fastest."""
+        buf = ctypes.create_string_buffer(1024)
+        check(lib.bm_pool_autotune(self.handle, cache_path.encode() if cache_path else None, buf,
+                                   len(buf)), "bm_pool_autotune")
+        return buf.value.decode()
 
     def empty_words(self, n: int | None = None) -> torch.Tensor:
         shape = (self.words,) if n is None else (n, self.words)

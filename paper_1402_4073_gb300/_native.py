@@ -28,6 +28,19 @@ class bm_pool_info_t(ctypes.Structure):
                 ("device_bytes", u64), ("dense_base", vp)]
 
 
+class bm_dense_config_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("variant", "threads", "stages", "ctas_per_sm",
+                                              "adder", "words_per_thread")]
+
+
+class bm_sparse_config_t(ctypes.Structure):
+    _fields_ = [("tile_rows", u32), ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+class bm_batch_config_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("ctas_per_sm", "adder", "words_per_thread")]
+
+
 class bm_server_config(ctypes.Structure):
     _fields_ = [("mem_budget", u64), ("max_batch", u32), ("max_inflight", u32), ("max_queue", u32),
                 ("batch_window_us", u32)]
@@ -49,13 +62,17 @@ SIGNATURES = {
     "bm_pool_info": (i32, [vp, ctypes.POINTER(bm_pool_info_t)]),
     "bm_pool_bitmap_cardinality": (i32, [vp, u32, P64]),
     "bm_pool_status": (i32, [vp]),
-    "bm_pool_set_dense_config": (i32, [vp, i32, i32, i32, i32, i32]),
+    "bm_pool_set_dense_config": (i32, [vp, ctypes.POINTER(bm_dense_config_t)]),
+    "bm_pool_get_dense_config": (i32, [vp, ctypes.POINTER(bm_dense_config_t)]),
+    "bm_pool_get_sparse_config": (i32, [vp, ctypes.POINTER(bm_sparse_config_t)]),
+    "bm_pool_get_batch_config": (i32, [vp, ctypes.POINTER(bm_batch_config_t)]),
+    "bm_pool_autotune": (i32, [vp, ctypes.c_char_p, ctypes.c_char_p, u64]),
     "bm_threshold_batch": (i32, [vp, vp, u32, vp, vp, vp]),
-    "bm_pool_set_batch_config": (i32, [vp, i32, i32]),
+    "bm_pool_set_batch_config": (i32, [vp, ctypes.POINTER(bm_batch_config_t)]),
     "bm_threshold": (i32, [vp, vp, u32, u32, vp, vp, vp]),
     "bm_symmetric": (i32, [vp, vp, u32, vp, vp, vp, vp]),
     "bm_cardinality": (i32, [vp, u64, vp, vp]),
-    "bm_pool_set_sparse_config": (i32, [vp, u32, i32, i32]),
+    "bm_pool_set_sparse_config": (i32, [vp, ctypes.POINTER(bm_sparse_config_t)]),
     "bm_query_run": (i32, [vp, vp, vp, vp, vp]),
     "bm_query_features": (i32, [vp, vp, vp]),
     "bm_pool_set_selector": (i32, [vp, vp, u64, vp, vp, u32]),

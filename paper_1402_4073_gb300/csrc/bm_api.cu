@@ -169,12 +169,23 @@ int bm_query_run(bm_pool* p, const bm_query* q, uint64_t* out_card, int32_t* cho
                       static_cast<cudaStream_t>(stream));
 }
 
-int bm_pool_set_sparse_config(bm_pool* p, uint32_t tile_rows, int threads, int ctas_per_sm) {
-    if (!p || tile_rows == 0 || tile_rows % kListTileRows || tile_rows > 65536) return BM_EINVAL;
-    if (threads < 64 || threads > 512 || threads % 32 || ctas_per_sm < 1 || ctas_per_sm > 8)
+int bm_pool_set_sparse_config(bm_pool* p, const bm_sparse_config_t* c) {
+    if (!p || !c || c->tile_rows == 0 || c->tile_rows % kListTileRows || c->tile_rows > 65536)
+        return BM_EINVAL;
+    if (c->threads < 64 || c->threads > 512 || c->threads % 32 || c->ctas_per_sm < 1 ||
+        c->ctas_per_sm > 8)
         return BM_EINVAL;
     std::lock_guard<std::mutex> lk(p->mu);
-    p->sparse_cfg = SparseConfig{tile_rows, threads, ctas_per_sm};
+    p->sparse_cfg = SparseConfig{c->tile_rows, c->threads, c->ctas_per_sm};
+    return BM_OK;
+}
+
+int bm_pool_get_sparse_config(bm_pool* p, bm_sparse_config_t* c) {
+    if (!p || !c) return BM_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    c->tile_rows = p->sparse_cfg.tile_rows;
+    c->threads = p->sparse_cfg.threads;
+    c->ctas_per_sm = p->sparse_cfg.ctas_per_sm;
     return BM_OK;
 }
 

@@ -78,12 +78,13 @@ __device__ __forceinline__ void block_card_add(unsigned long long card, unsigned
     }
 }
 
-template <int K, int G>
+template <int K, int G, int L>
 __global__ void __launch_bounds__(kBatchThreads, 2)
     dense_batch_kernel(BatchHeader* h, BatchPoolArgs pa) {
     __shared__ unsigned long long item_s;
     __shared__ unsigned long long part[kBatchThreads / 32];
-    const uint64_t ncols = (pa.words + 1) / 2;
+    constexpr uint64_t W = L / 2;  // 64-bit words per thread per input
+    const uint64_t ncols = (pa.words + W - 1) / W;
     const uint32_t nd = h->n_dense;
     const uint64_t total = h->dense_items;
     for (;;) {
@@ -100,11 +101,11 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
         if (col < ncols) {
             const Pred pred = d->pred;
             uint64_t* out = d->out;
-            uint32_t P[4][K];
-            zero_planes<K>(P);
-            count_column<K, G>(P, pa.base + 2 * col, d->ids, d->n, pa.stride_words);
+            uint32_t P[L][K];
+            zero_planes<K, L>(P);
+            count_column<K, G, L>(P, pa.base + W * col, d->ids, d->n, pa.stride_words);
             const bool vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
-            card = finish_column<K>(P, pred, pred.table, pa.r_bits, pa.words, out, col, vec_ok);
+            card = finish_column<K, L>(P, pred, pred.table, pa.r_bits, pa.words, out, col, vec_ok);
         }
         block_card_add(card, reinterpret_cast<unsigned long long*>(h->out_cards + qi), part);
     }
@@ -268,9 +269,10 @@ static int slot_reserve(bm_pool* p, BatchSlot& sl, size_t bytes) {
     return BM_OK;
 }
 
-static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, int adder,
-                     const BatchPoolArgs& pa, cudaGraphExec_t* out) {
-    const int key = K * 16 + adder;
+static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, const BatchPoolArgs& pa,
+                     cudaGraphExec_t* out) {
+    const int adder = b->cfg.adder, L = b->cfg.words_per_thread == 1 ? 2 : 4;
+    const int key = K * 64 + adder * 8 + L;
     auto it = sl.graphs.find(key);
     if (it != sl.graphs.end()) {
         *out = it->second;
@@ -306,18 +308,24 @@ static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, int adder,
     BM_CUDA_TRY(cudaFuncSetAttribute(sparse_batch_kernel,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sparse_batch_smem()));
-    if (adder == 1) {
-        if (K <= 5) return dense_fn(dense_batch_kernel<5, 8>);
-        if (K <= 9) return dense_fn(dense_batch_kernel<9, 8>);
-        if (K <= 11) return dense_fn(dense_batch_kernel<11, 8>);
-        if (K <= 13) return dense_fn(dense_batch_kernel<13, 8>);
-        return dense_fn(dense_batch_kernel<17, 8>);
+#define BM_BATCH_DISPATCH(LL)                                                      \
+    if (adder == 1) {                                                              \
+        if (K <= 5) return dense_fn(dense_batch_kernel<5, 8, LL>);                 \
+        if (K <= 9) return dense_fn(dense_batch_kernel<9, 8, LL>);                 \
+        if (K <= 11) return dense_fn(dense_batch_kernel<11, 8, LL>);               \
+        if (K <= 13) return dense_fn(dense_batch_kernel<13, 8, LL>);               \
+        return dense_fn(dense_batch_kernel<17, 8, LL>);                            \
+    }                                                                              \
+    if (K <= 5) return dense_fn(dense_batch_kernel<5, 16, LL>);                    \
+    if (K <= 9) return dense_fn(dense_batch_kernel<9, 16, LL>);                    \
+    if (K <= 11) return dense_fn(dense_batch_kernel<11, 16, LL>);                  \
+    if (K <= 13) return dense_fn(dense_batch_kernel<13, 16, LL>);                  \
+    return dense_fn(dense_batch_kernel<17, 16, LL>);
+    if (L == 4) {
+        BM_BATCH_DISPATCH(4)
     }
-    if (K <= 5) return dense_fn(dense_batch_kernel<5, 16>);
-    if (K <= 9) return dense_fn(dense_batch_kernel<9, 16>);
-    if (K <= 11) return dense_fn(dense_batch_kernel<11, 16>);
-    if (K <= 13) return dense_fn(dense_batch_kernel<13, 16>);
-    return dense_fn(dense_batch_kernel<17, 16>);
+    BM_BATCH_DISPATCH(2)
+#undef BM_BATCH_DISPATCH
 }
 
 // Learned choices for every AUTO query of a batch, on the device.
@@ -464,7 +472,8 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
     hh->nq = nq;
     hh->n_dense = (uint32_t)dense_list.size();
     hh->n_sparse = (uint32_t)sparse_list.size();
-    const uint64_t ncols = (p->words + 1) / 2;
+    const uint64_t wpt = b->cfg.words_per_thread == 1 ? 1 : 2;
+    const uint64_t ncols = (p->words + wpt - 1) / wpt;
     const uint64_t dense_tiles = (ncols + kBatchThreads - 1) / kBatchThreads;
     hh->dense_items = dense_tiles * dense_list.size();
     QueryDesc* hd = reinterpret_cast<QueryDesc*>(hb + o_desc);
@@ -506,7 +515,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
     const int K = planes_for(max_dense_n);
     const int kk = K <= 5 ? 5 : K <= 9 ? 9 : K <= 11 ? 11 : K <= 13 ? 13 : 17;
     cudaGraphExec_t ex = nullptr;
-    rc = graph_for(p, b, sl, kk, b->cfg.adder, pa, &ex);
+    rc = graph_for(p, b, sl, kk, pa, &ex);
     if (rc) return rc;
     BM_CUDA_TRY(cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, s));
     BM_CUDA_TRY(cudaGraphLaunch(ex, s));
@@ -515,18 +524,32 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
     return BM_OK;
 }
 
-extern "C" int bm_pool_set_batch_config(bm_pool* p, int ctas_per_sm, int adder) {
-    if (!p || ctas_per_sm < 1 || ctas_per_sm > 2 || adder < 0 || adder > 1) return BM_EINVAL;
+extern "C" int bm_pool_set_batch_config(bm_pool* p, const bm_batch_config_t* c) {
+    if (!p || !c || c->ctas_per_sm < 1 || c->ctas_per_sm > 2 || c->adder < 0 || c->adder > 1 ||
+        (c->words_per_thread != 1 && c->words_per_thread != 2))
+        return BM_EINVAL;
     std::lock_guard<std::mutex> lk(p->mu);
     BatchState* b = state(p);
-    if (b->cfg.ctas_per_sm != ctas_per_sm || b->cfg.adder != adder) {
+    if (b->cfg.ctas_per_sm != c->ctas_per_sm || b->cfg.adder != c->adder ||
+        b->cfg.words_per_thread != c->words_per_thread) {
         for (auto& sl : b->slots) {
             if (sl.used) cudaEventSynchronize(sl.ev);
             for (auto& kv : sl.graphs) cudaGraphExecDestroy(kv.second);
             sl.graphs.clear();
         }
     }
-    b->cfg.ctas_per_sm = ctas_per_sm;
-    b->cfg.adder = adder;
+    b->cfg.ctas_per_sm = c->ctas_per_sm;
+    b->cfg.adder = c->adder;
+    b->cfg.words_per_thread = c->words_per_thread;
+    return BM_OK;
+}
+
+extern "C" int bm_pool_get_batch_config(bm_pool* p, bm_batch_config_t* c) {
+    if (!p || !c) return BM_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    BatchState* b = state(p);
+    c->ctas_per_sm = b->cfg.ctas_per_sm;
+    c->adder = b->cfg.adder;
+    c->words_per_thread = b->cfg.words_per_thread;
     return BM_OK;
 }

@@ -43,20 +43,21 @@ __device__ __forceinline__ void load_table(const DenseArgs& a, uint32_t* tab, in
 // ---------------------------------------------------------------------------
 // variant 0: direct streaming loads
 
-template <int K, int G>
+template <int K, int G, int L>
 __global__ void __launch_bounds__(256, (K <= 13 ? 2 : 1)) csa_direct_kernel(DenseArgs a) {
     extern __shared__ uint32_t tab[];
     load_table(a, tab, threadIdx.x, blockDim.x);
     __syncthreads();
-    const uint64_t ncols = (a.words + 1) / 2;
+    constexpr uint64_t W = L / 2;  // 64-bit words per thread per input
+    const uint64_t ncols = (a.words + W - 1) / W;
     const bool vec_ok = ((reinterpret_cast<uintptr_t>(a.out) & 15u) == 0);
     unsigned long long card = 0;
     for (uint64_t col = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; col < ncols;
          col += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t P[4][K];
-        zero_planes<K>(P);
-        count_column<K, G>(P, a.base + 2 * col, a.ids, a.n, a.stride_words);
-        card += finish_column<K>(P, a.pred, tab, a.r_bits, a.words, a.out, col, vec_ok);
+        uint32_t P[L][K];
+        zero_planes<K, L>(P);
+        count_column<K, G, L>(P, a.base + W * col, a.ids, a.n, a.stride_words);
+        card += finish_column<K, L>(P, a.pred, tab, a.r_bits, a.words, a.out, col, vec_ok);
     }
     flush_card(card, a.card);
 }
@@ -129,10 +130,7 @@ __global__ void __launch_bounds__(NT + 32, 1) csa_bulk_kernel(DenseArgs a, int s
     bool ok = true;
     for (uint64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         uint32_t P[4][K];
-#pragma unroll
-        for (int l = 0; l < 4; ++l)
-#pragma unroll
-            for (int j = 0; j < K; ++j) P[l][j] = 0u;
+        zero_planes<K, 4>(P);
         for (uint32_t g = 0; g < ngroups; ++g, ++it) {
             const int s = (int)(it % (uint64_t)stages);
             // every lane waits; the warp proceeds only if all lanes saw the stage land
@@ -141,15 +139,15 @@ __global__ void __launch_bounds__(NT + 32, 1) csa_bulk_kernel(DenseArgs a, int s
                 ok = false;
                 break;
             }
-            const uint4* st = buf + (size_t)s * 16 * NT + tid;
+            const Slice<4>* st = reinterpret_cast<const Slice<4>*>(buf + (size_t)s * 16 * NT) + tid;
             const uint32_t nb = min(16u, a.n - g * 16);
             if (nb == 16) {
-                uint4 v[16];
+                Slice<4> v[16];
 #pragma unroll
                 for (int b = 0; b < 16; ++b) v[b] = st[b * NT];
-                add_group16<K>(P, v);
+                add_group<K, 4, 16>(P, v);
             } else {
-                add_partial<K>(P, nb, [&](uint32_t b) { return st[b * NT]; });
+                add_partial<K, 4>(P, nb, [&](uint32_t b) { return st[b * NT]; });
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
@@ -157,7 +155,7 @@ __global__ void __launch_bounds__(NT + 32, 1) csa_bulk_kernel(DenseArgs a, int s
         if (!ok) break;
         const uint64_t col = tile * NT + tid;
         if (col < ncols)
-            card += finish_column<K>(P, a.pred, tab, a.r_bits, a.words, a.out, col, vec_ok);
+            card += finish_column<K, 4>(P, a.pred, tab, a.r_bits, a.words, a.out, col, vec_ok);
     }
     if (ok) flush_card(card, a.card);
 }
@@ -168,10 +166,13 @@ int launch_k(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStrea
     const size_t tab_bytes = a.pred.mode == 2 ? (size_t)a.pred.table_words32 * 4 : 0;
     if (cfg.variant == 0) {
         const int threads = 256;
-        const uint64_t blocks_needed = (ncols + threads - 1) / threads;
+        const int L = cfg.words_per_thread == 1 ? 2 : 4;
+        const uint64_t cols = L == 4 ? ncols : a.words;
+        const uint64_t blocks_needed = (cols + threads - 1) / threads;
         const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);
         const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(blocks_needed, cap));
-        auto fn = cfg.adder == 1 ? csa_direct_kernel<K, 8> : csa_direct_kernel<K, 16>;
+        auto fn = L == 4 ? (cfg.adder == 1 ? csa_direct_kernel<K, 8, 4> : csa_direct_kernel<K, 16, 4>)
+                         : (cfg.adder == 1 ? csa_direct_kernel<K, 8, 2> : csa_direct_kernel<K, 16, 2>);
         if (tab_bytes > 48 * 1024)
             BM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)tab_bytes));

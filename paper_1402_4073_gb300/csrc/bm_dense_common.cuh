@@ -1,7 +1,7 @@
 // Column-level pieces of the dense bit-sliced counter shared by the
-// single-query kernels and the batch kernel: accumulate one 128-row column
-// of n inputs into counter planes, then evaluate the predicate, mask rows
-// >= r, store and popcount.
+// single-query kernels and the batch kernel: accumulate one column (64 or
+// 128 rows) of n inputs into counter planes, then evaluate the predicate,
+// mask rows >= r, store and popcount.
 #pragma once
 
 #include "bm_device.cuh"
@@ -9,127 +9,133 @@
 namespace bm {
 namespace dev {
 
-// Per-lane accumulation of a partial group (nb < group inputs) read by `get(b)`.
-template <int K, typename Get>
-__device__ __forceinline__ void add_partial(uint32_t (&P)[4][K], uint32_t nb, Get get) {
+// A thread's column is L 32-bit lanes (L = 4: a 16-byte slice, two 64-bit
+// words; L = 2: an 8-byte slice, one word) of every input.
+template <int L>
+struct Slice;
+template <>
+struct Slice<4> {
+    uint32_t v[4];
+};
+template <>
+struct Slice<2> {
+    uint32_t v[2];
+};
+
+// Streaming load of one slice (L1 allocation bypassed).
+template <int L>
+__device__ __forceinline__ Slice<L> ld_slice(const uint64_t* p) {
+    Slice<L> s;
+    if constexpr (L == 4) {
+        asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3])
+                     : "l"(p));
+    } else {
+        asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];"
+                     : "=r"(s.v[0]), "=r"(s.v[1])
+                     : "l"(p));
+    }
+    return s;
+}
+
+// Per-lane accumulation of a partial group (nb inputs) read by `get(b)`.
+template <int K, int L, typename Get>
+__device__ __forceinline__ void add_partial(uint32_t (&P)[L][K], uint32_t nb, Get get) {
     uint32_t b = 0;
     for (; b + 2 <= nb; b += 2) {
-        uint4 u = get(b), v = get(b + 1);
-        add2<K>(P[0], u.x, v.x);
-        add2<K>(P[1], u.y, v.y);
-        add2<K>(P[2], u.z, v.z);
-        add2<K>(P[3], u.w, v.w);
+        const auto u = get(b), v = get(b + 1);
+#pragma unroll
+        for (int l = 0; l < L; ++l) add2<K>(P[l], u.v[l], v.v[l]);
     }
     if (b < nb) {
-        uint4 u = get(b);
-        add1<K>(P[0], u.x);
-        add1<K>(P[1], u.y);
-        add1<K>(P[2], u.z);
-        add1<K>(P[3], u.w);
+        const auto u = get(b);
+#pragma unroll
+        for (int l = 0; l < L; ++l) add1<K>(P[l], u.v[l]);
     }
 }
 
-template <int K>
-__device__ __forceinline__ void add_group16(uint32_t (&P)[4][K], const uint4 (&v)[16]) {
-    uint32_t x[16];
+// One sideways-sum block of G (16 or 8) inputs on every lane.
+template <int K, int L, int G>
+__device__ __forceinline__ void add_group(uint32_t (&P)[L][K], const Slice<L> (&v)[G]) {
 #pragma unroll
-    for (int b = 0; b < 16; ++b) x[b] = v[b].x;
-    add16<K>(P[0], x);
+    for (int l = 0; l < L; ++l) {
+        uint32_t x[G];
 #pragma unroll
-    for (int b = 0; b < 16; ++b) x[b] = v[b].y;
-    add16<K>(P[1], x);
-#pragma unroll
-    for (int b = 0; b < 16; ++b) x[b] = v[b].z;
-    add16<K>(P[2], x);
-#pragma unroll
-    for (int b = 0; b < 16; ++b) x[b] = v[b].w;
-    add16<K>(P[3], x);
+        for (int b = 0; b < G; ++b) x[b] = v[b].v[l];
+        if constexpr (G == 16)
+            add16<K>(P[l], x);
+        else
+            add8<K>(P[l], x);
+    }
 }
 
-template <int K>
-__device__ __forceinline__ void add_group8(uint32_t (&P)[4][K], const uint4 (&v)[8]) {
-    uint32_t x[8];
+template <int K, int L>
+__device__ __forceinline__ void zero_planes(uint32_t (&P)[L][K]) {
 #pragma unroll
-    for (int b = 0; b < 8; ++b) x[b] = v[b].x;
-    add8<K>(P[0], x);
-#pragma unroll
-    for (int b = 0; b < 8; ++b) x[b] = v[b].y;
-    add8<K>(P[1], x);
-#pragma unroll
-    for (int b = 0; b < 8; ++b) x[b] = v[b].z;
-    add8<K>(P[2], x);
-#pragma unroll
-    for (int b = 0; b < 8; ++b) x[b] = v[b].w;
-    add8<K>(P[3], x);
-}
-
-template <int K>
-__device__ __forceinline__ void zero_planes(uint32_t (&P)[4][K]) {
-#pragma unroll
-    for (int l = 0; l < 4; ++l)
+    for (int l = 0; l < L; ++l)
 #pragma unroll
         for (int j = 0; j < K; ++j) P[l][j] = 0u;
 }
 
-// Count one 16-byte column (128 rows) of the n inputs ids[0..n) with direct
-// streaming loads, G (16 or 8) inputs per sideways-sum block.
-template <int K, int G>
-__device__ __forceinline__ void count_column(uint32_t (&P)[4][K], const uint64_t* colbase,
+// Count one column (L lanes of 32 rows) of the n inputs ids[0..n) with
+// direct streaming loads, G (16 or 8) inputs per sideways-sum block.
+template <int K, int G, int L>
+__device__ __forceinline__ void count_column(uint32_t (&P)[L][K], const uint64_t* colbase,
                                              const uint32_t* ids, uint32_t n,
                                              uint64_t stride_words) {
     uint32_t k = 0;
     for (; k + G <= n; k += G) {
-        uint4 v[G];
+        Slice<L> v[G];
 #pragma unroll
         for (int b = 0; b < G; ++b)
-            v[b] = ld_stream(colbase + (uint64_t)__ldg(ids + k + b) * stride_words);
-        if constexpr (G == 16)
-            add_group16<K>(P, v);
-        else
-            add_group8<K>(P, v);
+            v[b] = ld_slice<L>(colbase + (uint64_t)__ldg(ids + k + b) * stride_words);
+        add_group<K, L, G>(P, v);
     }
     if (k < n) {
         const uint32_t* rest = ids + k;
-        add_partial<K>(P, n - k, [&](uint32_t b) {
-            return ld_stream(colbase + (uint64_t)__ldg(rest + b) * stride_words);
+        add_partial<K, L>(P, n - k, [&](uint32_t b) {
+            return ld_slice<L>(colbase + (uint64_t)__ldg(rest + b) * stride_words);
         });
     }
 }
 
-// Predicate, tail mask, store and popcount of one 128-row column (words
-// 2*col and 2*col+1 of the output).
-template <int K>
-__device__ __forceinline__ uint32_t finish_column(const uint32_t (&P)[4][K], const Pred& pred,
+// Predicate, tail mask, store and popcount of one column: output words
+// (L/2)*col .. (L/2)*col + L/2 - 1.
+template <int K, int L>
+__device__ __forceinline__ uint32_t finish_column(const uint32_t (&P)[L][K], const Pred& pred,
                                                   const uint32_t* tab, uint64_t r_bits,
                                                   uint64_t words, uint64_t* out, uint64_t col,
                                                   bool vec_ok) {
-    uint32_t o0 = eval_pred<K>(P[0], pred, tab);
-    uint32_t o1 = eval_pred<K>(P[1], pred, tab);
-    uint32_t o2 = eval_pred<K>(P[2], pred, tab);
-    uint32_t o3 = eval_pred<K>(P[3], pred, tab);
-    uint64_t w0 = (uint64_t)o0 | ((uint64_t)o1 << 32);
-    uint64_t w1 = (uint64_t)o2 | ((uint64_t)o3 << 32);
-    const uint64_t i0 = 2 * col, i1 = i0 + 1;
+    constexpr int W = L / 2;
+    uint64_t w[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+        w[i] = (uint64_t)eval_pred<K>(P[2 * i], pred, tab) |
+               ((uint64_t)eval_pred<K>(P[2 * i + 1], pred, tab) << 32);
+    const uint64_t i0 = (uint64_t)W * col;
     const uint32_t tail = (uint32_t)(r_bits & 63u);
-    const uint64_t last = words - 1;
     if (tail) {
         const uint64_t m = (1ull << tail) - 1ull;
-        if (i0 == last) w0 &= m;
-        if (i1 == last) w1 &= m;
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+            if (i0 + i == words - 1) w[i] &= m;
     }
-    if (i1 < words) {
-        if (vec_ok) {
-            asm volatile("st.global.v2.u64 [%0], {%1, %2};" ::"l"(out + i0), "l"(w0), "l"(w1)
-                         : "memory");
-        } else {
-            out[i0] = w0;
-            out[i1] = w1;
+    if constexpr (W == 2) {
+        if (i0 + 1 < words) {
+            if (vec_ok) {
+                asm volatile("st.global.v2.u64 [%0], {%1, %2};" ::"l"(out + i0), "l"(w[0]),
+                             "l"(w[1])
+                             : "memory");
+            } else {
+                out[i0] = w[0];
+                out[i0 + 1] = w[1];
+            }
+            return (uint32_t)(__popcll(w[0]) + __popcll(w[1]));
         }
-        return (uint32_t)(__popcll(w0) + __popcll(w1));
     }
     if (i0 < words) {
-        out[i0] = w0;
-        return (uint32_t)__popcll(w0);
+        out[i0] = w[0];
+        return (uint32_t)__popcll(w[0]);
     }
     return 0;
 }

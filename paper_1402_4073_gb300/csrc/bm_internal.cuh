@@ -75,7 +75,8 @@ struct DenseConfig {
     int threads;   // consumer threads per CTA
     int stages;    // pipeline depth (variant 1)
     int ctas_per_sm;
-    int adder = 0;  // sideways-sum block: 0 = 16 inputs, 1 = 8 inputs (variant 0)
+    int adder = 0;             // sideways-sum block: 0 = 16 inputs, 1 = 8 inputs (variant 0)
+    int words_per_thread = 2;  // 64-bit words per thread per input: 2 or 1 (variant 0)
 };
 
 int launch_dense(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStream_t s);

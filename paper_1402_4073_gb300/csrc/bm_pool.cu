@@ -348,14 +348,31 @@ int bm_pool_info(const bm_pool* p, bm_pool_info_t* out) {
     return BM_OK;
 }
 
-int bm_pool_set_dense_config(bm_pool* p, int variant, int threads, int stages, int ctas_per_sm,
-                             int adder) {
-    if (!p || variant < 0 || variant > 1 || ctas_per_sm < 1 || ctas_per_sm > 8) return BM_EINVAL;
-    if (adder < 0 || adder > 1 || (variant == 1 && adder != 0)) return BM_EINVAL;
-    if (variant == 1 && (!(threads == 64 || threads == 128) || stages < 2 || stages > 8))
+int bm_pool_set_dense_config(bm_pool* p, const bm_dense_config_t* c) {
+    if (!p || !c || c->variant < 0 || c->variant > 1 || c->ctas_per_sm < 1 || c->ctas_per_sm > 8)
+        return BM_EINVAL;
+    if (c->adder < 0 || c->adder > 1 || (c->variant == 1 && c->adder != 0)) return BM_EINVAL;
+    if ((c->words_per_thread != 1 && c->words_per_thread != 2) ||
+        (c->variant == 1 && c->words_per_thread != 2))
+        return BM_EINVAL;
+    if (c->variant == 1 && (!(c->threads == 64 || c->threads == 128) || c->stages < 2 ||
+                            c->stages > 8))
         return BM_EINVAL;
     std::lock_guard<std::mutex> lk(p->mu);
-    p->dense_cfg = DenseConfig{variant, variant == 0 ? 256 : threads, stages, ctas_per_sm, adder};
+    p->dense_cfg = DenseConfig{c->variant, c->variant == 0 ? 256 : c->threads, c->stages,
+                               c->ctas_per_sm, c->adder, c->words_per_thread};
+    return BM_OK;
+}
+
+int bm_pool_get_dense_config(bm_pool* p, bm_dense_config_t* c) {
+    if (!p || !c) return BM_EINVAL;
+    std::lock_guard<std::mutex> lk(p->mu);
+    c->variant = p->dense_cfg.variant;
+    c->threads = p->dense_cfg.threads;
+    c->stages = p->dense_cfg.stages;
+    c->ctas_per_sm = p->dense_cfg.ctas_per_sm;
+    c->adder = p->dense_cfg.adder;
+    c->words_per_thread = p->dense_cfg.words_per_thread;
     return BM_OK;
 }
 
