@@ -156,14 +156,15 @@ def cpu_sample_time(words, queries, r_bits, budget_s: float):
     return nbytes / dt, nw, dt
 
 
-def bench_batched(bm, datagen, passes: int = 2):
+def bench_batched(bm, datagen, passes: int = 2, small: bool = False):
     """Mixed batch (2000 x 2^24 pool, 4096 queries): plain one query per
-    launch vs one batched graph replay; queries/s of each."""
+    launch vs one batched graph replay; queries/s of each.  small: 400 x 2^22
+    pool and 512 queries (for profiling only)."""
     import torch
-    r_bits = 1 << 24
-    words, _ = datagen.mixed_pool(2000, r_bits)
-    queries = datagen.mixed_queries(4096, 2000)
-    pool = bm.Pool(r_bits, 2000)
+    r_bits, nbm, nq = (1 << 22, 400, 512) if small else (1 << 24, 2000, 4096)
+    words, _ = datagen.mixed_pool(nbm, r_bits)
+    queries = datagen.mixed_queries(nq, nbm, nmax=min(1000, nbm))
+    pool = bm.Pool(r_bits, nbm)
     pool.put_dense(words)
     del words
     outs = [pool.empty_words() for _ in queries]
@@ -197,8 +198,8 @@ def bench_batched(bm, datagen, passes: int = 2):
     pool.status()
     logical = sum(query_bytes(q.n, r_bits) for q in queries)
     pool.close()
-    return {"workload": "mixed: 2000 x 2^24 pool (densities log-uniform [1e-4,0.5]), 4096 queries "
-                        "N log-uniform [3,1000], 10% intervals",
+    return {"workload": f"mixed: {nbm} x 2^{r_bits.bit_length() - 1} pool (densities log-uniform "
+                        f"[1e-4,0.5]), {nq} queries N log-uniform [3,{min(1000, nbm)}], 10% intervals",
             "plain_queries_per_s": round(len(queries) / t_plain, 1),
             "batched_queries_per_s": round(len(queries) / t_batch, 1),
             "speedup": round(t_plain / t_batch, 3),
@@ -207,18 +208,21 @@ def bench_batched(bm, datagen, passes: int = 2):
             "cardinalities_equal": same, "timing": f"best of {passes} passes, CUDA events"}
 
 
-def bench_selector(bm, datagen, n_train: int = 600):
+def bench_selector(bm, datagen, n_train: int = 600, small: bool = False):
     """Sparse workload (5000 x 2^24, dense + lists; 2000 queries): train the
     selector on its own timings of separate training queries, then report
     time lost on the 2000 workload queries for the network and the fixed
     rule, and queries/s of the batched+selected form vs plain dense."""
     import torch
     from paper_1402_4073_gb300 import selector
-    r_bits = 1 << 24
-    words, flat, offs, _ = datagen.sparse_pool(5000, r_bits)
-    test_q = datagen.sparse_queries(2000, 5000)
-    train_q = datagen.sparse_queries(n_train, 5000, stream=datagen.STREAM_SPARSE + (7 << 32))
-    pool = bm.Pool(r_bits, 5000)
+    r_bits, nbm, nq = (1 << 22, 800, 300) if small else (1 << 24, 5000, 2000)
+    if small:
+        n_train = 100
+    words, flat, offs, _ = datagen.sparse_pool(nbm, r_bits)
+    test_q = datagen.sparse_queries(nq, nbm, nmax=min(4096, nbm))
+    train_q = datagen.sparse_queries(n_train, nbm, nmax=min(4096, nbm),
+                                     stream=datagen.STREAM_SPARSE + (7 << 32))
+    pool = bm.Pool(r_bits, nbm)
     pool.put_dense(words)
     pool.put_positions(flat, offs)
     del words, flat
@@ -255,8 +259,9 @@ def bench_selector(bm, datagen, n_train: int = 600):
     pool.status()
     pool.close()
     out = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in res.items()}
-    out.update({"workload": "sparse: 5000 x 2^24 pool (densities log-uniform [1e-5,1e-2], dense + "
-                            "position lists), 2000 queries N log-uniform [2,4096], theta<=min(N,64)",
+    out.update({"workload": f"sparse: {nbm} x 2^{r_bits.bit_length() - 1} pool (densities log-uniform "
+                            f"[1e-5,1e-2], dense + position lists), {nq} queries N log-uniform "
+                            f"[2,{min(4096, nbm)}], theta<=min(N,64)",
                 "train_queries": n_train, "train_steps": 3000, "train_s": round(train_s, 2),
                 "final_train_loss": round(model.final_loss, 5),
                 "plain_dense_queries_per_s": round(len(test_q) / t_plain, 1),
@@ -267,24 +272,29 @@ def bench_selector(bm, datagen, n_train: int = 600):
     return out
 
 
-def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds: float = 0.8):
+def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds: float = 0.8,
+                  small: bool = False):
     """Serving loop on the 10,000 x 2^22 pool: Poisson arrivals at each
-    offered rate; p50/p99 latency and achieved queries/s."""
+    offered rate; p50/p99 latency and achieved queries/s.  small: 1000
+    bitmaps, two rates, 300 requests each (for profiling only)."""
     from paper_1402_4073_gb300.serve import Server, summarize
-    r_bits = 1 << 22
-    words, _ = datagen.serving_pool(10000, r_bits)
-    pool = bm.Pool(r_bits, 10000)
+    r_bits, nbm = 1 << 22, (1000 if small else 10000)
+    if small:
+        rates, seconds = (1000, 10000), 0.03
+    words, _ = datagen.serving_pool(nbm, r_bits)
+    pool = bm.Pool(r_bits, nbm)
     pool.put_dense(words)
     del words
     out = []
     slot = (pool.words * 8 + 255) // 256 * 256
     with Server(pool, mem_budget=4096 * slot, max_batch=512, max_inflight=2) as srv:
         # warm-up: graph capture and caches
-        warm = datagen.serving_queries(256, 50000.0, stream=datagen.STREAM_SERVING + (9 << 32))
+        warm = datagen.serving_queries(256, 50000.0, pool=nbm, nmax=min(4096, nbm),
+                                       stream=datagen.STREAM_SERVING + (9 << 32))
         srv.replay(warm, [q.arrival_s for q in warm])
         for k, rate in enumerate(rates):
-            n = int(min(40000, max(500, rate * seconds)))
-            qs = datagen.serving_queries(n, float(rate),
+            n = int(min(40000, max(300 if small else 500, rate * seconds)))
+            qs = datagen.serving_queries(n, float(rate), pool=nbm, nmax=min(4096, nbm),
                                          stream=datagen.STREAM_SERVING + ((10 + k) << 32))
             res = srv.replay(qs, [q.arrival_s for q in qs])
             summ = summarize(res, float(rate))
@@ -293,8 +303,8 @@ def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds:
         st = srv.stats()
     pool.status()
     pool.close()
-    return {"workload": "serving: 10000 x 2^22 pool (densities log-uniform [1e-5,0.5]), Poisson "
-                        "arrivals, N log-uniform [2,4096], theta uniform [1,N]",
+    return {"workload": f"serving: {nbm} x 2^22 pool (densities log-uniform [1e-5,0.5]), Poisson "
+                        f"arrivals, N log-uniform [2,{min(4096, nbm)}], theta uniform [1,N]",
             "admission": "4096 result slots (2 GiB); max batch 512; 2 batches in flight",
             "mean_batch": round(st["batched_queries"] / max(1, st["batches"]), 1),
             "rates": out}
@@ -310,9 +320,11 @@ def run_reference(args):
     datagen.build()
     words, queries = datagen.config2(R_BITS, N)
     cores = os.cpu_count() or 1
-    # one step = the four queries over a fixed prefix of words, sized to ~1 s
+    # one step = the four queries over a fixed prefix of words, sized so that
+    # the whole run (warm-up + timed steps) takes about two minutes
+    per_step_s = min(1.0, 120.0 / max(1, args.steps + args.warmup))
     _, nw, dt = cpu_sample_time(words, queries, R_BITS, 2.0)
-    nw = max(64, int(nw * min(8.0, 1.0 / max(dt, 1e-3))))
+    nw = max(64, int(nw * min(8.0, per_step_s / max(dt, 1e-3))))
     nw = min(nw, words.shape[1])
     for _ in range(args.warmup):
         for q in queries:
@@ -353,6 +365,8 @@ def main():
                     help="variant,threads,stages,ctas_per_sm[,adder]: skip the variant search")
     ap.add_argument("--parts", default="dense,batch,selector,serving",
                     help="comma list of dense, batch, selector, serving")
+    ap.add_argument("--small", action="store_true",
+                    help="scaled-down batch/selector/serving workloads (profiling only)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     global R_BITS, WORKLOAD
@@ -473,11 +487,11 @@ def main():
     extra = {}
     parts = args.parts.split(",")
     if "batch" in parts:
-        extra["batched"] = bench_batched(bm, datagen)
+        extra["batched"] = bench_batched(bm, datagen, small=args.small)
     if "selector" in parts:
-        extra["selector"] = bench_selector(bm, datagen)
+        extra["selector"] = bench_selector(bm, datagen, small=args.small)
     if "serving" in parts:
-        extra["serving"] = bench_serving(bm, datagen)
+        extra["serving"] = bench_serving(bm, datagen, small=args.small)
 
     if rank == 0:
         print(json.dumps({

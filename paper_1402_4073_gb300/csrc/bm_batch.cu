@@ -398,7 +398,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
         int rc = validate_ids(p, qi.ids, qi.n, qi.path);
         if (!rc) rc = query_truth(&qi, truth[i]);
         if (rc) return rc;
-        total_ids += qi.n;
+        total_ids += (qi.n + 3) & ~3u;  // each query's ids start 16-byte aligned
         if (qi.path == BM_PATH_AUTO) {
             if (!p->sel_params.empty() && p->sel_outputs == kCandidates) {
                 auto_idx.push_back(i);
@@ -495,7 +495,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
             hd[i].pred.table = reinterpret_cast<const uint32_t*>(db + o_tab) + tab_pos;
             tab_pos += preds[i].table_words32;
         }
-        id_pos += q[i].n;
+        id_pos += (q[i].n + 3) & ~3u;
     }
     if (!dense_list.empty())
         memcpy(hb + o_dl, dense_list.data(), 4 * dense_list.size());

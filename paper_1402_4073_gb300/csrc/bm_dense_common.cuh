@@ -78,24 +78,44 @@ __device__ __forceinline__ void zero_planes(uint32_t (&P)[L][K]) {
 }
 
 // Count one column (L lanes of 32 rows) of the n inputs ids[0..n) with
-// direct streaming loads, G (16 or 8) inputs per sideways-sum block.
+// direct streaming loads, G (16 or 8) inputs per sideways-sum block.  ids
+// must be 16-byte aligned: full blocks read their ids four at a time.  The
+// last n mod G inputs go through 8-input blocks padded with zero inputs,
+// which costs less than rippling each input through every plane.
 template <int K, int G, int L>
 __device__ __forceinline__ void count_column(uint32_t (&P)[L][K], const uint64_t* colbase,
                                              const uint32_t* ids, uint32_t n,
                                              uint64_t stride_words) {
     uint32_t k = 0;
     for (; k + G <= n; k += G) {
+        uint32_t id[G];
+#pragma unroll
+        for (int i = 0; i < G / 4; ++i) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4*>(ids + k) + i);
+            id[4 * i] = q.x;
+            id[4 * i + 1] = q.y;
+            id[4 * i + 2] = q.z;
+            id[4 * i + 3] = q.w;
+        }
         Slice<L> v[G];
 #pragma unroll
-        for (int b = 0; b < G; ++b)
-            v[b] = ld_slice<L>(colbase + (uint64_t)__ldg(ids + k + b) * stride_words);
+        for (int b = 0; b < G; ++b) v[b] = ld_slice<L>(colbase + (uint64_t)id[b] * stride_words);
         add_group<K, L, G>(P, v);
     }
-    if (k < n) {
-        const uint32_t* rest = ids + k;
-        add_partial<K, L>(P, n - k, [&](uint32_t b) {
-            return ld_slice<L>(colbase + (uint64_t)__ldg(rest + b) * stride_words);
-        });
+    while (k < n) {
+        const uint32_t m = min(8u, n - k);
+        Slice<L> v[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            if ((uint32_t)b < m) {
+                v[b] = ld_slice<L>(colbase + (uint64_t)__ldg(ids + k + b) * stride_words);
+            } else {
+#pragma unroll
+                for (int l = 0; l < L; ++l) v[b].v[l] = 0u;
+            }
+        }
+        add_group<K, L, 8>(P, v);
+        k += m;
     }
 }
 
