@@ -1,0 +1,64 @@
+"""Row sharding across ranks, on CPU with two gloo ranks: each rank answers
+the query on its rows (the oracle stands in for the per-rank GPU path); the
+gathered bitmap and the summed cardinality equal the whole-pool answer."""
+from __future__ import annotations
+
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank(rank, world, port, r_bits, q):
+    import torch.distributed as dist
+
+    import datagen
+    import oracle
+    from paper_1402_4073_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        words = datagen.bernoulli(datagen.STREAM_TESTS + 17000, r_bits, np.linspace(0.05, 0.6, 12))
+        ids = np.array([0, 3, 5, 7, 7, 11, 2], dtype=np.uint32)
+        local, rows = shard.shard_words(words, r_bits, rank, world)
+        part, card = oracle.threshold(local, ids, rows, 3)
+        total = shard.sum_cardinality(card)
+        full = shard.gather_words(part, r_bits, world)
+        want, want_card = oracle.threshold(words, ids, r_bits, 3)
+        q.put((rank, bool(np.array_equal(full, want)), total == want_card))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("r_bits", [64 * 1000, 64 * 1001 + 13, 70])
+def test_two_rank_row_shards(r_bits):
+    import __graft_entry__
+    __graft_entry__.cuda_build_module().build()  # the package loads libbm.so on import
+    from paper_1402_4073_gb300 import shard
+    # ranges tile the rows exactly, on word boundaries
+    for world in (1, 2, 3, 8):
+        spans = [shard.row_range(r_bits, g, world) for g in range(world)]
+        assert spans[0][0] == 0 and spans[-1][1] == r_bits
+        for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+            assert a1 == b0 and a0 % 64 == 0
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(g, 2, port, r_bits, q)) for g in range(2)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    assert all(ok_words and ok_card for _, ok_words, ok_card in results), results
