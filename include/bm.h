@@ -155,11 +155,12 @@ int bm_pool_get_dense_config(bm_pool* pool, bm_dense_config_t* cfg);
 /*
  * Shape of the sparse (ScanCount) kernel: tile_rows rows of counters per CTA
  * (a multiple of 8192, at most 65536), `threads` per CTA (64..512, a
- * multiple of 32), ctas_per_sm (1..8).  BM_EINVAL outside these ranges.
+ * multiple of 32), ctas_per_sm (1..8), unroll = list slices each warp keeps
+ * in flight (4 or 8).  BM_EINVAL outside these ranges.
  */
 typedef struct bm_sparse_config_t {
     uint32_t tile_rows;
-    int32_t threads, ctas_per_sm;
+    int32_t threads, ctas_per_sm, unroll;
 } bm_sparse_config_t;
 int bm_pool_set_sparse_config(bm_pool* pool, const bm_sparse_config_t* cfg);
 int bm_pool_get_sparse_config(bm_pool* pool, bm_sparse_config_t* cfg);

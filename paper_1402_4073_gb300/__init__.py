@@ -147,8 +147,8 @@ class Pool:
         check(lib.bm_pool_set_dense_config(self.handle, ctypes.byref(c)), "bm_pool_set_dense_config")
 
     def set_sparse_config(self, tile_rows: int = 32768, threads: int = 512,
-                          ctas_per_sm: int = 2) -> None:
-        c = _native.bm_sparse_config_t(tile_rows, threads, ctas_per_sm)
+                          ctas_per_sm: int = 2, unroll: int = 4) -> None:
+        c = _native.bm_sparse_config_t(tile_rows, threads, ctas_per_sm, unroll)
         check(lib.bm_pool_set_sparse_config(self.handle, ctypes.byref(c)),
               "bm_pool_set_sparse_config")
 

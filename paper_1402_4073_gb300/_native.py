@@ -34,7 +34,8 @@ class bm_dense_config_t(ctypes.Structure):
 
 
 class bm_sparse_config_t(ctypes.Structure):
-    _fields_ = [("tile_rows", u32), ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+    _fields_ = [("tile_rows", u32), ("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("unroll", ctypes.c_int32)]
 
 
 class bm_batch_config_t(ctypes.Structure):

@@ -173,10 +173,10 @@ int bm_pool_set_sparse_config(bm_pool* p, const bm_sparse_config_t* c) {
     if (!p || !c || c->tile_rows == 0 || c->tile_rows % kListTileRows || c->tile_rows > 65536)
         return BM_EINVAL;
     if (c->threads < 64 || c->threads > 512 || c->threads % 32 || c->ctas_per_sm < 1 ||
-        c->ctas_per_sm > 8)
+        c->ctas_per_sm > 8 || (c->unroll != 4 && c->unroll != 8))
         return BM_EINVAL;
     std::lock_guard<std::mutex> lk(p->mu);
-    p->sparse_cfg = SparseConfig{c->tile_rows, c->threads, c->ctas_per_sm};
+    p->sparse_cfg = SparseConfig{c->tile_rows, c->threads, c->ctas_per_sm, c->unroll};
     return BM_OK;
 }
 
@@ -186,6 +186,7 @@ int bm_pool_get_sparse_config(bm_pool* p, bm_sparse_config_t* c) {
     c->tile_rows = p->sparse_cfg.tile_rows;
     c->threads = p->sparse_cfg.threads;
     c->ctas_per_sm = p->sparse_cfg.ctas_per_sm;
+    c->unroll = p->sparse_cfg.unroll;
     return BM_OK;
 }
 

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 1)
         const uint32_t sub = tile_rows / kListTileRows;
         const uint64_t t0 = tile * sub;
         const uint64_t t1 = (t0 + sub < pa.tiles_per_list) ? t0 + sub : (uint64_t)pa.tiles_per_list;
-        count_tile<16>(cnt, scratch, d->ids, n, pa.positions, pa.list_begin, pa.tile_index,
+        count_tile<16, 4>(cnt, scratch, d->ids, n, pa.positions, pa.list_begin, pa.tile_index,
                        pa.tiles_per_list, t0, t1, (uint32_t)rlo);
         __syncthreads();
         const uint32_t lanes = (uint32_t)((rhi - rlo + 31) / 32);

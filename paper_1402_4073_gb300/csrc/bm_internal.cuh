@@ -100,6 +100,7 @@ struct SparseConfig {
     uint32_t tile_rows;  // multiple of kListTileRows
     int threads;
     int ctas_per_sm;
+    int unroll = 4;      // list slices a warp has in flight: 4 or 8
 };
 
 int launch_sparse(const SparseArgs& a, const SparseConfig& cfg, int sm_count, cudaStream_t s);

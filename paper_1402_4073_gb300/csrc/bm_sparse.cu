@@ -40,8 +40,8 @@ __device__ void build_truth(const Pred& pr, uint32_t n, uint32_t* tab, uint32_t 
     }
 }
 
-template <int BITS>  // counter width: 8 or 16
-__global__ void __launch_bounds__(512) scancount_kernel(SparseArgs a) {
+template <int BITS, int U>  // counter width: 8 or 16; slices in flight per warp
+__global__ void __launch_bounds__(512, 3) scancount_kernel(SparseArgs a) {
     extern __shared__ __align__(16) uint32_t sm[];
     constexpr uint32_t kPer = 32 / BITS;  // counters per 32-bit word
     const uint32_t tab_words = (a.n + 1 + 31) / 32;
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(512) scancount_kernel(SparseArgs a) {
         __syncthreads();
         const uint64_t t0 = tile * sub;
         const uint64_t t1 = (t0 + sub < a.tiles_per_list) ? t0 + sub : (uint64_t)a.tiles_per_list;
-        count_tile<BITS>(cnt, scratch, a.ids, a.n, a.positions, a.list_begin, a.tile_index,
+        count_tile<BITS, U>(cnt, scratch, a.ids, a.n, a.positions, a.list_begin, a.tile_index,
                          a.tiles_per_list, t0, t1, (uint32_t)lo);
         __syncthreads();
         // 32 rows per thread -> one 32-bit output lane
@@ -106,7 +106,9 @@ int launch_sparse(const SparseArgs& a, const SparseConfig& cfg, int sm_count, cu
         BM_CUDA_TRY(cudaGetLastError());
         return BM_OK;
     };
-    return bits == 8 ? go(scancount_kernel<8>) : go(scancount_kernel<16>);
+    if (cfg.unroll >= 8)
+        return bits == 8 ? go(scancount_kernel<8, 8>) : go(scancount_kernel<16, 8>);
+    return bits == 8 ? go(scancount_kernel<8, 4>) : go(scancount_kernel<16, 4>);
 }
 
 }  // namespace bm

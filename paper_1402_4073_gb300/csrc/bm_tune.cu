@@ -15,7 +15,7 @@ namespace {
 
 struct Tuned {
     bm_dense_config_t dense{0, 256, 4, 2, 0, 2};
-    bm_sparse_config_t sparse{32768, 512, 2};
+    bm_sparse_config_t sparse{32768, 512, 2, 4};
     bm_batch_config_t batch{2, 0, 2};
     bool has_sparse = false;
 };
@@ -47,8 +47,8 @@ bool cache_load(const char* path, const std::string& key, Tuned& t) {
                        &x.dense.stages, &x.dense.ctas_per_sm, &x.dense.adder,
                        &x.dense.words_per_thread) == 6)
                 ok |= 1;
-            else if (sscanf(tag.c_str(), "sparse=%u,%d,%d", &x.sparse.tile_rows, &x.sparse.threads,
-                            &x.sparse.ctas_per_sm) == 3) {
+            else if (sscanf(tag.c_str(), "sparse=%u,%d,%d,%d", &x.sparse.tile_rows,
+                            &x.sparse.threads, &x.sparse.ctas_per_sm, &x.sparse.unroll) == 4) {
                 x.has_sparse = true;
             } else if (sscanf(tag.c_str(), "batch=%d,%d,%d", &x.batch.ctas_per_sm, &x.batch.adder,
                               &x.batch.words_per_thread) == 3)
@@ -71,7 +71,8 @@ void cache_store(const char* path, const std::string& key, const Tuned& t) {
             t.dense.words_per_thread, t.batch.ctas_per_sm, t.batch.adder,
             t.batch.words_per_thread);
     if (t.has_sparse)
-        fprintf(f, " sparse=%u,%d,%d", t.sparse.tile_rows, t.sparse.threads, t.sparse.ctas_per_sm);
+        fprintf(f, " sparse=%u,%d,%d,%d", t.sparse.tile_rows, t.sparse.threads,
+                t.sparse.ctas_per_sm, t.sparse.unroll);
     fprintf(f, "\n");
     fclose(f);
 }
@@ -168,8 +169,9 @@ extern "C" int bm_pool_autotune(bm_pool* p, const char* cache_path, char* report
             best = 1e30;
             for (uint32_t tile : {16384u, 32768u, 65536u})
                 for (int th : {256, 512})
-                    for (int ct : {1, 2, 4}) {
-                        bm_sparse_config_t c{tile, th, ct};
+                    for (int ct : {1, 2, 4})
+                    for (int un : {4, 8}) {
+                        bm_sparse_config_t c{tile, th, ct, un};
                         if (bm_pool_set_sparse_config(p, &c)) continue;
                         rc = time_us(s, [&] { return bm_query_run(p, &sq, cards, nullptr, s); }, &tt);
                         if (rc) break;
@@ -180,7 +182,8 @@ extern "C" int bm_pool_autotune(bm_pool* p, const char* cache_path, char* report
                     }
             t.has_sparse = true;
             rep << " sparse=" << t.sparse.tile_rows << "," << t.sparse.threads << ","
-                << t.sparse.ctas_per_sm << " (" << best << " us, n=" << sq.n << ")";
+                << t.sparse.ctas_per_sm << "," << t.sparse.unroll << " (" << best << " us, n="
+                << sq.n << ")";
         }
         // batch: 32 dense queries over rotating subsets of up to 64 bitmaps
         if (!rc) {
