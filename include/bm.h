@@ -136,8 +136,9 @@ int bm_pool_status(bm_pool* pool);
  *   variant 0: direct streaming loads, 256 threads per CTA; `threads` and
  *              `stages` ignored.
  *   variant 1: bulk-copy (TMA) pipeline through shared memory with
- *              `threads` consumer threads per CTA (64 or 128) and `stages`
- *              pipeline stages (2..8) of 16 bitmaps each.
+ *              `threads` consumer threads per CTA (64, 128 or 256) and
+ *              `stages` pipeline stages (2..8, fewer if shared memory is
+ *              short) of 16 bitmaps each.
  * ctas_per_sm (1..8) caps the persistent grid at ctas_per_sm x SM count.
  * adder: layout of the adder tree (Sec. 4.3 "Sideways Sum"): 0 = blocks of
  *   16 inputs through 15 full adders, 1 = blocks of 8 inputs through 7

@@ -14,9 +14,9 @@
 //  * variant 0 ("direct"): each thread issues 16 streaming 128-bit loads per
 //    step, coalesced across the warp (consecutive threads read consecutive
 //    16-byte slices of the same bitmap).
-//  * variant 1 ("bulk"): one producer thread per CTA moves each
-//    (tile, group of 16 bitmaps) into a shared-memory stage with bulk copies
-//    (cp.async.bulk, the non-tensor TMA form) completing on an mbarrier; the
+//  * variant 1 ("bulk"): a producer warp moves each (tile, group of 16
+//    bitmaps) into a shared-memory stage with bulk copies (cp.async.bulk, the
+//    non-tensor TMA form; one lane per bitmap) completing on an mbarrier; the
 //    consumer warps read 128-bit slices from shared memory.  Stages are
 //    recycled through a second mbarrier per stage.  All waits are bounded.
 #include <algorithm>
@@ -91,8 +91,9 @@ __global__ void __launch_bounds__(NT + 32, 1) csa_bulk_kernel(DenseArgs a, int s
     const uint64_t stride_bytes = a.stride_words * 8;
 
     if (warp == kConsumerWarps) {
-        // producer: one elected thread issues the bulk copies
-        if (lane != 0) return;
+        // producer warp: lane 0 waits for free stages and posts the expected
+        // bytes; lane b then issues the bulk copy of bitmap b of the group,
+        // so the 16 copies of a stage go out in parallel
         const uint64_t pol = policy_evict_first();
         uint64_t it = 0;
         bool ok = true;
@@ -101,25 +102,30 @@ __global__ void __launch_bounds__(NT + 32, 1) csa_bulk_kernel(DenseArgs a, int s
             const uint32_t bytes = (uint32_t)min((uint64_t)NT * 16, stride_bytes - off);
             for (uint32_t g = 0; g < ngroups; ++g, ++it) {
                 const int s = (int)(it % (uint64_t)stages);
-                if (it >= (uint64_t)stages &&
-                    !mbar_wait_bounded(&empty[s], (uint32_t)((it / stages - 1) & 1), a.err)) {
+                bool free_stage = true;
+                if (lane == 0 && it >= (uint64_t)stages)
+                    free_stage = mbar_wait_bounded(&empty[s], (uint32_t)((it / stages - 1) & 1), a.err);
+                if (!__shfl_sync(0xFFFFFFFFu, free_stage, 0)) {
                     ok = false;
                     break;
                 }
                 const uint32_t nb = min(16u, a.n - g * 16);
-                mbar_arrive_expect_tx(&full[s], nb * bytes);
-                const uint32_t* ids = a.ids + g * 16;
-                for (uint32_t b = 0; b < nb; ++b) {
+                if (lane == 0) mbar_arrive_expect_tx(&full[s], nb * bytes);
+                __syncwarp();
+                if ((uint32_t)lane < nb) {
                     const uint8_t* src = reinterpret_cast<const uint8_t*>(a.base) +
-                                         (uint64_t)__ldg(ids + b) * stride_bytes + off;
-                    bulk_g2s(buf + ((size_t)s * 16 + b) * NT, src, bytes, &full[s], pol);
+                                         (uint64_t)__ldg(a.ids + g * 16 + lane) * stride_bytes + off;
+                    bulk_g2s(buf + ((size_t)s * 16 + lane) * NT, src, bytes, &full[s], pol);
                 }
+                __syncwarp();
             }
         }
         // every issued copy must land before this CTA may exit
-        const uint64_t first = it > (uint64_t)stages ? it - stages : 0;
-        for (uint64_t j = first; j < it; ++j)
-            mbar_wait_bounded(&full[j % stages], (uint32_t)((j / stages) & 1), a.err);
+        if (lane == 0) {
+            const uint64_t first = it > (uint64_t)stages ? it - stages : 0;
+            for (uint64_t j = first; j < it; ++j)
+                mbar_wait_bounded(&full[j % stages], (uint32_t)((j / stages) & 1), a.err);
+        }
         return;
     }
 
@@ -199,7 +205,8 @@ int launch_k(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStrea
         return BM_OK;
     };
     if (cfg.threads <= 64) return run(csa_bulk_kernel<K, 64>, 64);
-    return run(csa_bulk_kernel<K, 128>, 128);
+    if (cfg.threads <= 128) return run(csa_bulk_kernel<K, 128>, 128);
+    return run(csa_bulk_kernel<K, 256>, 256);
 }
 
 }  // namespace

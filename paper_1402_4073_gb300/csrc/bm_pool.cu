@@ -355,7 +355,8 @@ int bm_pool_set_dense_config(bm_pool* p, const bm_dense_config_t* c) {
     if ((c->words_per_thread != 1 && c->words_per_thread != 2) ||
         (c->variant == 1 && c->words_per_thread != 2))
         return BM_EINVAL;
-    if (c->variant == 1 && (!(c->threads == 64 || c->threads == 128) || c->stages < 2 ||
+    if (c->variant == 1 && (!(c->threads == 64 || c->threads == 128 || c->threads == 256) ||
+                            c->stages < 2 ||
                             c->stages > 8))
         return BM_EINVAL;
     std::lock_guard<std::mutex> lk(p->mu);

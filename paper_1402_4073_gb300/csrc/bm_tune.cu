@@ -144,8 +144,8 @@ extern "C" int bm_pool_autotune(bm_pool* p, const char* cache_path, char* report
         q.path = BM_PATH_DENSE;
         std::vector<bm_dense_config_t> dense_c = {
             {0, 256, 4, 2, 0, 2}, {0, 256, 4, 3, 0, 2}, {0, 256, 4, 2, 1, 2}, {0, 256, 4, 3, 1, 2},
-            {0, 256, 4, 2, 0, 1}, {0, 256, 4, 4, 0, 1}, {0, 256, 4, 4, 1, 1}, {1, 128, 4, 1, 0, 2},
-            {1, 128, 3, 1, 0, 2}, {1, 64, 6, 2, 0, 2}};
+            {0, 256, 4, 2, 0, 1}, {0, 256, 4, 4, 0, 1}, {0, 256, 4, 4, 1, 1}, {1, 256, 3, 1, 0, 2},
+            {1, 256, 2, 1, 0, 2}, {1, 128, 4, 1, 0, 2}, {1, 64, 6, 2, 0, 2}};
         double best = 1e30, tt = 0;
         for (auto& c : dense_c) {
             if (bm_pool_set_dense_config(p, &c)) continue;
