@@ -35,7 +35,8 @@ N = 256
 WORKLOAD = "large dense: N=256 bitmaps x r=2^26 rows, densities max(0.5/k,1e-4) in geometric runs; " \
            "queries theta=2,128,255 and interval [2,10]"
 METRIC = "threshold-query input GB/s"
-DENSE_SOURCES = ["paper_1402_4073_gb300/csrc/bm_dense.cu", "paper_1402_4073_gb300/csrc/bm_device.cuh"]
+DENSE_SOURCES = ["paper_1402_4073_gb300/csrc/bm_dense.cu", "paper_1402_4073_gb300/csrc/bm_device.cuh",
+                 "paper_1402_4073_gb300/csrc/bm_dense_common.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dense_csa_n256_r2e26.txt")
 
 
