@@ -168,6 +168,7 @@ def bench_batched(bm, datagen, passes: int = 2, small: bool = False):
     pool = bm.Pool(r_bits, nbm)
     pool.put_dense(words)
     del words
+    tune = pool.autotune()
     outs = [pool.empty_words() for _ in queries]
     cards_plain = torch.zeros(len(queries), dtype=torch.int64, device="cuda")
     cards_batch = torch.zeros(len(queries), dtype=torch.int64, device="cuda")
@@ -206,7 +207,8 @@ def bench_batched(bm, datagen, passes: int = 2, small: bool = False):
             "speedup": round(t_plain / t_batch, 3),
             "plain_logical_GBps": round(logical / t_plain / 1e9, 1),
             "batched_logical_GBps": round(logical / t_batch / 1e9, 1),
-            "cardinalities_equal": same, "timing": f"best of {passes} passes, CUDA events"}
+            "cardinalities_equal": same, "timing": f"best of {passes} passes, CUDA events",
+            "autotune": tune}
 
 
 def bench_selector(bm, datagen, n_train: int = 600, small: bool = False):
@@ -227,6 +229,7 @@ def bench_selector(bm, datagen, n_train: int = 600, small: bool = False):
     pool.put_dense(words)
     pool.put_positions(flat, offs)
     del words, flat
+    tune = pool.autotune()
     ftr, ttr = selector.collect(pool, train_q, reps=3)
     fte, tte = selector.collect(pool, test_q, reps=3)
     t0 = time.perf_counter()
@@ -269,7 +272,7 @@ def bench_selector(bm, datagen, n_train: int = 600, small: bool = False):
                 "batched_selected_queries_per_s": round(len(test_q) / t_sel, 1),
                 "speedup": round(t_plain / t_sel, 3),
                 "sparse_share": round(float((chosen[-1] == bm.PATH_SPARSE).mean()), 3),
-                "cardinalities_equal": same})
+                "cardinalities_equal": same, "autotune": tune})
     return out
 
 
@@ -286,6 +289,7 @@ def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds:
     pool = bm.Pool(r_bits, nbm)
     pool.put_dense(words)
     del words
+    tune = pool.autotune()
     out = []
     slot = (pool.words * 8 + 255) // 256 * 256
     with Server(pool, mem_budget=4096 * slot, max_batch=512, max_inflight=2) as srv:
@@ -308,7 +312,7 @@ def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds:
                         f"arrivals, N log-uniform [2,{min(4096, nbm)}], theta uniform [1,N]",
             "admission": "4096 result slots (2 GiB); max batch 512; 2 batches in flight",
             "mean_batch": round(st["batched_queries"] / max(1, st["batches"]), 1),
-            "rates": out}
+            "autotune": tune, "rates": out}
 
 
 def run_reference(args):

@@ -142,7 +142,9 @@ int bm_pool_status(bm_pool* pool);
  * ctas_per_sm (1..8) caps the persistent grid at ctas_per_sm x SM count.
  * adder: layout of the adder tree (Sec. 4.3 "Sideways Sum"): 0 = blocks of
  *   16 inputs through 15 full adders, 1 = blocks of 8 inputs through 7
- *   (fewer live registers, one more carry ripple per 8 inputs); variant 0.
+ *   (fewer live registers, one more carry ripple per 8 inputs), 2 = blocks
+ *   of 32 inputs (two 16-input trees joined by one more full adder: half
+ *   the carry ripples; needs words_per_thread 2); variant 0.
  * words_per_thread: 64-bit words of each input a thread owns, 2 (16-byte
  *   loads) or 1 (8-byte loads, twice the threads per row range); variant 0.
  * BM_EINVAL for values outside these ranges.
@@ -168,7 +170,7 @@ int bm_pool_get_sparse_config(bm_pool* pool, bm_sparse_config_t* cfg);
 
 /*
  * Shape of the batch kernel: dense persistent CTAs per SM (1 or 2), adder
- * layout and words per thread (as for the dense kernel).
+ * layout (0, 1 or 2) and words per thread (as for the dense kernel).
  */
 typedef struct bm_batch_config_t {
     int32_t ctas_per_sm, adder, words_per_thread;

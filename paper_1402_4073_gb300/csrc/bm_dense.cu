@@ -177,7 +177,10 @@ int launch_k(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStrea
         const uint64_t blocks_needed = (cols + threads - 1) / threads;
         const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);
         const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(blocks_needed, cap));
-        auto fn = L == 4 ? (cfg.adder == 1 ? csa_direct_kernel<K, 8, 4> : csa_direct_kernel<K, 16, 4>)
+        constexpr int G32 = K >= 6 ? 32 : 16;  // 32-input blocks need a sixth plane
+        auto fn = L == 4 ? (cfg.adder == 1   ? csa_direct_kernel<K, 8, 4>
+                            : cfg.adder == 2 ? csa_direct_kernel<K, G32, 4>
+                                             : csa_direct_kernel<K, 16, 4>)
                          : (cfg.adder == 1 ? csa_direct_kernel<K, 8, 2> : csa_direct_kernel<K, 16, 2>);
         if (tab_bytes > 48 * 1024)
             BM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,

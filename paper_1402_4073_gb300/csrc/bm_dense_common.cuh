@@ -78,7 +78,7 @@ __device__ __forceinline__ void zero_planes(uint32_t (&P)[L][K]) {
 }
 
 // Count one column (L lanes of 32 rows) of the n inputs ids[0..n) with
-// direct streaming loads, G (16 or 8) inputs per sideways-sum block.  ids
+// direct streaming loads, G (32, 16 or 8) inputs per sideways-sum block.  ids
 // must be 16-byte aligned: full blocks read their ids four at a time.  The
 // last n mod G inputs go through 8-input blocks padded with zero inputs,
 // which costs less than rippling each input through every plane.
@@ -87,20 +87,52 @@ __device__ __forceinline__ void count_column(uint32_t (&P)[L][K], const uint64_t
                                              const uint32_t* ids, uint32_t n,
                                              uint64_t stride_words) {
     uint32_t k = 0;
-    for (; k + G <= n; k += G) {
-        uint32_t id[G];
+    if constexpr (G == 32) {
+        // two sixteen-input trees per step, joined at plane 4
+        for (; k + 32 <= n; k += 32) {
+            uint32_t s16[2][L];
 #pragma unroll
-        for (int i = 0; i < G / 4; ++i) {
+            for (int h = 0; h < 2; ++h) {
+                uint32_t id[16];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint4 q = __ldg(reinterpret_cast<const uint4*>(ids + k + 16 * h) + i);
+                    id[4 * i] = q.x;
+                    id[4 * i + 1] = q.y;
+                    id[4 * i + 2] = q.z;
+                    id[4 * i + 3] = q.w;
+                }
+                Slice<L> v[16];
+#pragma unroll
+                for (int b = 0; b < 16; ++b)
+                    v[b] = ld_slice<L>(colbase + (uint64_t)id[b] * stride_words);
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    uint32_t x[16];
+#pragma unroll
+                    for (int b = 0; b < 16; ++b) x[b] = v[b].v[l];
+                    s16[h][l] = add16_carry<K>(P[l], x);
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < L; ++l) add32_join<K>(P[l], s16[0][l], s16[1][l]);
+        }
+    }
+    constexpr int GB = G == 32 ? 16 : G;  // block size for what is left
+    for (; k + GB <= n; k += GB) {
+        uint32_t id[GB];
+#pragma unroll
+        for (int i = 0; i < GB / 4; ++i) {
             const uint4 q = __ldg(reinterpret_cast<const uint4*>(ids + k) + i);
             id[4 * i] = q.x;
             id[4 * i + 1] = q.y;
             id[4 * i + 2] = q.z;
             id[4 * i + 3] = q.w;
         }
-        Slice<L> v[G];
+        Slice<L> v[GB];
 #pragma unroll
-        for (int b = 0; b < G; ++b) v[b] = ld_slice<L>(colbase + (uint64_t)id[b] * stride_words);
-        add_group<K, L, G>(P, v);
+        for (int b = 0; b < GB; ++b) v[b] = ld_slice<L>(colbase + (uint64_t)id[b] * stride_words);
+        add_group<K, L, GB>(P, v);
     }
     while (k < n) {
         const uint32_t m = min(8u, n - k);

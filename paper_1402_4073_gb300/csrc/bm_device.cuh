@@ -63,6 +63,39 @@ __device__ __forceinline__ void add2(uint32_t (&P)[K], uint32_t x0, uint32_t x1)
 // (Sec. 4.3, "Sideways Sum"): planes 0..3 act as carry-save accumulators,
 // 15 full adders per 16 inputs, and the single weight-16 carry is rippled
 // into planes 4.. .  Requires K >= 5.
+// The sixteen-input tree of add16 without its last ripple: returns the
+// weight-16 carry.
+template <int K>
+__device__ __forceinline__ uint32_t add16_carry(uint32_t (&P)[K], const uint32_t (&x)[16]) {
+    uint32_t twosA, twosB, foursA, foursB, eightsA, eightsB, sixteens;
+    csa(twosA, P[0], P[0], x[0], x[1]);
+    csa(twosB, P[0], P[0], x[2], x[3]);
+    csa(foursA, P[1], P[1], twosA, twosB);
+    csa(twosA, P[0], P[0], x[4], x[5]);
+    csa(twosB, P[0], P[0], x[6], x[7]);
+    csa(foursB, P[1], P[1], twosA, twosB);
+    csa(eightsA, P[2], P[2], foursA, foursB);
+    csa(twosA, P[0], P[0], x[8], x[9]);
+    csa(twosB, P[0], P[0], x[10], x[11]);
+    csa(foursA, P[1], P[1], twosA, twosB);
+    csa(twosA, P[0], P[0], x[12], x[13]);
+    csa(twosB, P[0], P[0], x[14], x[15]);
+    csa(foursB, P[1], P[1], twosA, twosB);
+    csa(eightsB, P[2], P[2], foursA, foursB);
+    csa(sixteens, P[3], P[3], eightsA, eightsB);
+    return sixteens;
+}
+
+// Thirty-two inputs as two sixteen-input trees whose weight-16 carries meet
+// plane 4 in one more full adder; only the weight-32 carry ripples, into
+// planes 5.. .  Requires K >= 6.
+template <int K>
+__device__ __forceinline__ void add32_join(uint32_t (&P)[K], uint32_t s16a, uint32_t s16b) {
+    uint32_t t32;
+    csa(t32, P[4], P[4], s16a, s16b);
+    ripple<K>(P, t32, 5);
+}
+
 template <int K>
 __device__ __forceinline__ void add16(uint32_t (&P)[K], const uint32_t (&x)[16]) {
     uint32_t twosA, twosB, foursA, foursB, eightsA, eightsB, sixteens;

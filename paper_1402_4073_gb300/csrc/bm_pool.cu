@@ -351,7 +351,8 @@ int bm_pool_info(const bm_pool* p, bm_pool_info_t* out) {
 int bm_pool_set_dense_config(bm_pool* p, const bm_dense_config_t* c) {
     if (!p || !c || c->variant < 0 || c->variant > 1 || c->ctas_per_sm < 1 || c->ctas_per_sm > 8)
         return BM_EINVAL;
-    if (c->adder < 0 || c->adder > 1 || (c->variant == 1 && c->adder != 0)) return BM_EINVAL;
+    if (c->adder < 0 || c->adder > 2 || (c->variant == 1 && c->adder != 0)) return BM_EINVAL;
+    if (c->adder == 2 && c->words_per_thread != 2) return BM_EINVAL;
     if ((c->words_per_thread != 1 && c->words_per_thread != 2) ||
         (c->variant == 1 && c->words_per_thread != 2))
         return BM_EINVAL;

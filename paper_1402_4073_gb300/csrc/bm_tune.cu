@@ -144,6 +144,7 @@ extern "C" int bm_pool_autotune(bm_pool* p, const char* cache_path, char* report
         q.path = BM_PATH_DENSE;
         std::vector<bm_dense_config_t> dense_c = {
             {0, 256, 4, 2, 0, 2}, {0, 256, 4, 3, 0, 2}, {0, 256, 4, 2, 1, 2}, {0, 256, 4, 3, 1, 2},
+            {0, 256, 4, 2, 2, 2},
             {0, 256, 4, 2, 0, 1}, {0, 256, 4, 4, 0, 1}, {0, 256, 4, 4, 1, 1}, {1, 256, 3, 1, 0, 2},
             {1, 256, 2, 1, 0, 2}, {1, 128, 4, 1, 0, 2}, {1, 64, 6, 2, 0, 2}};
         double best = 1e30, tt = 0;
@@ -203,7 +204,7 @@ extern "C" int bm_pool_autotune(bm_pool* p, const char* cache_path, char* report
             }
             best = 1e30;
             for (int ct : {1, 2})
-                for (int ad : {0, 1})
+                for (int ad : {0, 1, 2})
                     for (int w : {2, 1}) {
                         bm_batch_config_t c{ct, ad, w};
                         if (bm_pool_set_batch_config(p, &c)) continue;

@@ -46,11 +46,12 @@ def collect(pool: Pool, queries, reps: int = 3, stream=None):
     out = pool.empty_words()
     card = torch.zeros(1, dtype=torch.int64, device=out.device)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+    saved = pool.configs()["sparse"]
     for c, (path, tile) in enumerate(CANDIDATES):
         if path == PATH_SPARSE:
             if info["lists_loaded"] == 0:
                 continue
-            pool.set_sparse_config(tile, 512, 2)
+            pool.set_sparse_config(tile, saved["threads"], saved["ctas_per_sm"], saved["unroll"])
         for i, q in enumerate(queries):
             query_run(pool, q, out, card, path=path, stream=stream)  # warm-up
             for r in range(reps):
@@ -60,7 +61,7 @@ def collect(pool: Pool, queries, reps: int = 3, stream=None):
             stream.synchronize()
             times[i, c] = np.median([ev[2 * r].elapsed_time(ev[2 * r + 1]) * 1e3
                                      for r in range(reps)])
-    pool.set_sparse_config(32768, 512, 2)
+    pool.set_sparse_config(**saved)
     return feats, times
 
 

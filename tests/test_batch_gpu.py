@@ -43,7 +43,8 @@ def _batch(bm, pool, queries, paths=None):
     return [bm.to_numpy_words(o) for o in outs], cards.cpu().numpy(), chosen
 
 
-@pytest.mark.parametrize("batch_cfg", [(2, 0, 2), (1, 0, 2), (2, 1, 2), (2, 0, 1), (1, 1, 1)])
+@pytest.mark.parametrize("batch_cfg", [(2, 0, 2), (1, 0, 2), (2, 1, 2), (2, 0, 1), (1, 1, 1),
+                                       (2, 2, 2)])
 def test_batch_matches_oracle(bm, oracle_lib, dg, mixed, batch_cfg):
     r_bits, words, flat, offs, queries = mixed
     with bm.Pool(r_bits, words.shape[0]) as pool:

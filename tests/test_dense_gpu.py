@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 # every feeding variant of the dense kernel: (variant, threads, stages, ctas_per_sm)
 # (variant, threads, stages, ctas_per_sm, adder, words_per_thread)
 VARIANTS = [(0, 256, 4, 2, 0, 2), (1, 256, 3, 1, 0, 2), (0, 256, 4, 2, 1, 1), (1, 64, 3, 2, 0, 2),
-            (1, 128, 2, 1, 0, 2), (0, 256, 4, 3, 1, 2), (0, 256, 4, 2, 0, 1), (1, 128, 4, 1, 0, 2)]
+            (1, 128, 2, 1, 0, 2), (0, 256, 4, 3, 1, 2), (0, 256, 4, 2, 0, 1), (1, 128, 4, 1, 0, 2),
+            (0, 256, 4, 2, 2, 2)]
 
 
 @pytest.fixture(scope="module")
