@@ -315,16 +315,26 @@ def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds:
             "autotune": tune, "rates": out}
 
 
+def oracle_threads() -> int:
+    """Threads the oracle's OpenMP loops use."""
+    try:
+        return int(os.environ.get("OMP_NUM_THREADS", ""))
+    except ValueError:
+        return os.cpu_count() or 1
+
+
 def run_reference(args):
     rank, world, _ = dist_setup("gloo")
     if rank != 0:
         return
+    # the launcher limits each rank to one thread; rank 0 alone runs, on every core
+    os.environ["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
     import datagen
     import oracle
     oracle.build()
     datagen.build()
     words, queries = datagen.config2(R_BITS, N)
-    cores = os.cpu_count() or 1
+    cores = oracle_threads()
     # one step = the four queries over a fixed prefix of words, sized so that
     # the whole run (warm-up + timed steps) takes about two minutes
     per_step_s = min(1.0, 120.0 / max(1, args.steps + args.warmup))
@@ -483,7 +493,7 @@ def main():
         import oracle
         oracle.build()
         bps, nw, dt = cpu_sample_time(words, queries, R_BITS, args.cpu_budget)
-        cpu = {"value": round(bps / 1e9, 4), "unit": "GB/s", "cores": os.cpu_count() or 1,
+        cpu = {"value": round(bps / 1e9, 4), "unit": "GB/s", "cores": oracle_threads(),
                "kind": "oracle",
                "sample": f"the 4 queries over the first {nw} of {words.shape[1]} words "
                          f"({64 * nw} rows), {dt:.1f} s"}

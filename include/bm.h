@@ -300,6 +300,8 @@ typedef struct bm_server_stats_t {
     uint32_t free_slots, total_slots;
     uint32_t max_batch_seen;
     int32_t last_error;       /* last launch error (BM_OK if none) */
+    uint64_t cancelled;       /* removed by bm_server_cancel before admission */
+    uint64_t expired;         /* deadline passed before admission */
 } bm_server_stats_t;
 
 /*
@@ -323,6 +325,23 @@ int bm_server_destroy(bm_server* server);
  * identifies the request.
  */
 int bm_server_submit(bm_server* server, const bm_query* q, uint64_t* ticket);
+
+/*
+ * As bm_server_submit, with a deadline: if the request is still waiting for
+ * admission deadline_us microseconds after submission, it completes without
+ * running and bm_server_wait / bm_server_result report BM_ETIMEOUT for it
+ * (release it as any other).  deadline_us = 0: no deadline.
+ */
+int bm_server_submit_deadline(bm_server* server, const bm_query* q, uint64_t deadline_us,
+                              uint64_t* ticket);
+
+/*
+ * Withdraw a request that is still waiting for admission (its ticket is
+ * forgotten).  BM_EBUSY if it was already admitted (it then runs to
+ * completion and must be collected or released), BM_ERANGE for an unknown
+ * ticket.
+ */
+int bm_server_cancel(bm_server* server, uint64_t ticket);
 
 /* Wait up to timeout_ms for a request: BM_OK, BM_ETIMEOUT, or its launch error. */
 int bm_server_wait(bm_server* server, uint64_t ticket, uint32_t timeout_ms);

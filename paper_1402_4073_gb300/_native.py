@@ -50,7 +50,8 @@ class bm_server_config(ctypes.Structure):
 class bm_server_stats_t(ctypes.Structure):
     _fields_ = [("submitted", u64), ("completed", u64), ("refused", u64), ("batches", u64),
                 ("batched_queries", u64), ("waiting", u32), ("free_slots", u32),
-                ("total_slots", u32), ("max_batch_seen", u32), ("last_error", ctypes.c_int32)]
+                ("total_slots", u32), ("max_batch_seen", u32), ("last_error", ctypes.c_int32),
+                ("cancelled", u64), ("expired", u64)]
 
 
 # name -> (restype, argtypes)
@@ -87,6 +88,8 @@ SIGNATURES = {
     "bm_server_destroy": (i32, [vp]),
     "bm_server_submit": (i32, [vp, vp, ctypes.POINTER(u64)]),
     "bm_server_wait": (i32, [vp, u64, u32]),
+    "bm_server_submit_deadline": (i32, [vp, vp, u64, ctypes.POINTER(u64)]),
+    "bm_server_cancel": (i32, [vp, u64]),
     "bm_server_result": (i32, [vp, u64, vp, vp, vp, vp, vp]),
     "bm_server_release": (i32, [vp, u64]),
     "bm_server_stats": (i32, [vp, ctypes.POINTER(bm_server_stats_t)]),

@@ -38,6 +38,7 @@ struct Request {
     int32_t path = 0;
     uint64_t card = 0;
     Clock::time_point t_submit, t_launch, t_done;
+    Clock::time_point deadline = Clock::time_point::max();  // drop if still waiting after this
     bool done = false;
 };
 
@@ -72,6 +73,7 @@ struct bm_server {
 
     // statistics
     uint64_t submitted = 0, completed = 0, refused = 0, batches_run = 0, batched_queries = 0;
+    uint64_t cancelled = 0, expired = 0;
     uint32_t max_batch_seen = 0;
     int last_error = BM_OK;
 };
@@ -119,7 +121,9 @@ void scheduler(bm_server* s) {
     cudaSetDevice(s->pool->device);
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
-        s->cv_sched.wait(lk, [&] {
+        // wakes on submissions, completions and releases; at least every
+        // millisecond while requests wait, to expire their deadlines
+        s->cv_sched.wait_for(lk, std::chrono::milliseconds(1), [&] {
             if (s->stop) return true;
             if (s->waiting.empty() || s->free_slots.empty()) return false;
             for (auto& b : s->batches)
@@ -133,6 +137,25 @@ void scheduler(bm_server* s) {
             std::this_thread::sleep_for(std::chrono::microseconds(s->cfg.batch_window_us));
             lk.lock();
             if (s->stop) break;
+        }
+        {
+            // requests whose deadline passed while they waited complete as expired
+            const auto now = Clock::now();
+            bool expired = false;
+            for (auto it = s->waiting.begin(); it != s->waiting.end();) {
+                if ((*it)->deadline <= now) {
+                    Request* r = *it;
+                    r->done = true;
+                    r->t_launch = r->t_done = now;
+                    r->path = BM_ETIMEOUT;
+                    s->expired += 1;
+                    it = s->waiting.erase(it);
+                    expired = true;
+                } else {
+                    ++it;
+                }
+            }
+            if (expired) s->cv_done.notify_all();
         }
         for (auto& b : s->batches) {
             if (b.busy || s->waiting.empty() || s->free_slots.empty()) continue;
@@ -250,6 +273,11 @@ int bm_server_destroy(bm_server* s) {
 }
 
 int bm_server_submit(bm_server* s, const bm_query* q, uint64_t* ticket) {
+    return bm_server_submit_deadline(s, q, 0, ticket);
+}
+
+int bm_server_submit_deadline(bm_server* s, const bm_query* q, uint64_t deadline_us,
+                              uint64_t* ticket) {
     if (!s || !q || !ticket || !q->ids || q->n == 0 || q->n > BM_N_MAX || q->reserved)
         return BM_EINVAL;
     if (q->kind > BM_KIND_TABLE || q->path < BM_PATH_AUTO || q->path > BM_PATH_SPARSE)
@@ -268,6 +296,7 @@ int bm_server_submit(bm_server* s, const bm_query* q, uint64_t* ticket) {
     r->q.ids = r->ids.data();
     r->q.table = r->table.empty() ? nullptr : r->table.data();
     r->t_submit = Clock::now();
+    if (deadline_us) r->deadline = r->t_submit + std::chrono::microseconds(deadline_us);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->waiting.size() >= s->cfg.max_queue) {
@@ -319,6 +348,24 @@ int bm_server_result(bm_server* s, uint64_t ticket, uint64_t* host_words, uint64
     if (queue_us) *queue_us = us_since(r->t_submit, r->t_launch);
     if (path) *path = r->path;
     return rc;
+}
+
+int bm_server_cancel(bm_server* s, uint64_t ticket) {
+    if (!s) return BM_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return BM_ERANGE;
+        Request* r = it->second;
+        auto w = std::find(s->waiting.begin(), s->waiting.end(), r);
+        if (w == s->waiting.end()) return BM_EBUSY;  // admitted: it runs to completion
+        s->waiting.erase(w);
+        s->reqs.erase(it);
+        s->cancelled += 1;
+        delete r;
+    }
+    s->cv_sched.notify_one();
+    return BM_OK;
 }
 
 int bm_server_release(bm_server* s, uint64_t ticket) {
@@ -401,6 +448,8 @@ int bm_server_stats(bm_server* s, bm_server_stats_t* out) {
     out->free_slots = (uint32_t)s->free_slots.size();
     out->total_slots = s->n_slots;
     out->max_batch_seen = s->max_batch_seen;
+    out->cancelled = s->cancelled;
+    out->expired = s->expired;
     out->last_error = s->last_error;
     return BM_OK;
 }

@@ -39,11 +39,15 @@ class Server:
     def __exit__(self, *exc):
         self.close()
 
-    def submit(self, query, path: int | None = None) -> int:
+    def submit(self, query, path: int | None = None, deadline_us: int = 0) -> int:
         q, keep = _q_from(query, None, path)
         t = ctypes.c_uint64()
-        check(lib.bm_server_submit(self.handle, ctypes.byref(q), ctypes.byref(t)), "bm_server_submit")
+        check(lib.bm_server_submit_deadline(self.handle, ctypes.byref(q), deadline_us,
+                                            ctypes.byref(t)), "bm_server_submit")
         return int(t.value)
+
+    def cancel(self, ticket: int) -> None:
+        check(lib.bm_server_cancel(self.handle, ticket), "bm_server_cancel")
 
     def wait(self, ticket: int, timeout_ms: int = 10000) -> int:
         return lib.bm_server_wait(self.handle, ticket, timeout_ms)

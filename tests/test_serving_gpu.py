@@ -131,3 +131,33 @@ def test_wait_timeout_self_test(bm, served):
     pool.status()  # cleared
     o, c = _alone(bm, pool, queries[0])
     assert c >= 0
+
+
+def test_cancel_and_deadline(bm, served):
+    """A waiting request can be withdrawn; one whose deadline passes while it
+    waits for memory completes as expired; admitted requests still run."""
+    from paper_1402_4073_gb300.serve import Server
+    pool, words, queries, r_bits = served
+    with Server(pool, mem_budget=_slots(pool, 1), max_batch=4, max_inflight=1) as srv:
+        first = srv.submit(queries[0])
+        assert srv.wait(first, 20000) == 0  # holds the only slot
+        t_cancel = srv.submit(queries[1])
+        t_expire = srv.submit(queries[2], deadline_us=2000)
+        t_keep = srv.submit(queries[3])
+        srv.cancel(t_cancel)
+        with pytest.raises(bm.BMError) as e:
+            srv.cancel(t_cancel)
+        assert e.value.code == bm.BM_ERANGE
+        assert srv.wait(t_expire, 20000) == bm.BM_ETIMEOUT
+        with pytest.raises(bm.BMError) as e:
+            srv.result(t_expire)
+        assert e.value.code == bm.BM_ETIMEOUT
+        srv.release(t_expire)
+        with pytest.raises(bm.BMError) as e:
+            srv.cancel(first)  # already admitted and done
+        assert e.value.code == bm.BM_EBUSY
+        srv.release(first)
+        assert srv.wait(t_keep, 20000) == 0
+        srv.release(t_keep)
+        st = srv.stats()
+        assert st["cancelled"] == 1 and st["expired"] == 1 and st["free_slots"] == 1
