@@ -317,22 +317,20 @@ def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds:
 
 def oracle_threads() -> int:
     """Threads the oracle's OpenMP loops use."""
-    try:
-        return int(os.environ.get("OMP_NUM_THREADS", ""))
-    except ValueError:
-        return os.cpu_count() or 1
+    import oracle
+    return oracle.threads()
 
 
 def run_reference(args):
     rank, world, _ = dist_setup("gloo")
     if rank != 0:
         return
-    # the launcher limits each rank to one thread; rank 0 alone runs, on every core
-    os.environ["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
     import datagen
     import oracle
     oracle.build()
     datagen.build()
+    # a launcher may limit each rank to one thread; rank 0 alone runs, on every core
+    oracle.set_threads(os.cpu_count() or 1)
     words, queries = datagen.config2(R_BITS, N)
     cores = oracle_threads()
     # one step = the four queries over a fixed prefix of words, sized so that
@@ -492,6 +490,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
+        oracle.set_threads(os.cpu_count() or 1)
         bps, nw, dt = cpu_sample_time(words, queries, R_BITS, args.cpu_budget)
         cpu = {"value": round(bps / 1e9, 4), "unit": "GB/s", "cores": oracle_threads(),
                "kind": "oracle",

@@ -50,6 +50,10 @@ def _L():
         lib.oracle_symmetric.restype = None
         lib.oracle_scancount.argtypes = [vp, vp, vp, u32, u64, u64, vp, u64, u64, vp, vp]
         lib.oracle_scancount.restype = None
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_threads.restype = None
+        lib.oracle_get_threads.argtypes = []
+        lib.oracle_get_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -73,6 +77,15 @@ def _prep(pool: np.ndarray, ids):
     if len(ids):
         assert int(ids.max()) < pool.shape[0], "id out of range"
     return pool, ids
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops."""
+    _L().oracle_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(_L().oracle_get_threads())
 
 
 def cardinality(words: np.ndarray, r_bits: int) -> int:

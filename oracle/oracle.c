@@ -20,9 +20,17 @@
  * The counting is literal: one integer counter per row, incremented once per
  * input that has the row's bit set, then compared.  No word-level tricks.
  */
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Threads of the oracle's OpenMP loops (the host's cores by default). */
+void oracle_set_threads(int n) {
+    if (n > 0) omp_set_num_threads(n);
+}
+
+int oracle_get_threads(void) { return omp_get_max_threads(); }
 
 static inline int oracle_bit(const uint64_t *words, uint64_t i) {
     return (int)((words[i / 64] >> (i % 64)) & 1u);
