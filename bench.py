@@ -174,12 +174,17 @@ def bench_batched(bm, datagen, passes: int = 2, small: bool = False):
     cards_batch = torch.zeros(len(queries), dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
 
+    singles = [bm.PreparedQuery(pool, q, outs[i], bm.PATH_DENSE) for i, q in enumerate(queries)]
+    card_views = [cards_plain[i:i + 1] for i in range(len(queries))]
+
     def plain():
-        for i, q in enumerate(queries):
-            bm.query_run(pool, q, outs[i], cards_plain[i:i + 1], path=bm.PATH_DENSE)
+        for sq, c in zip(singles, card_views):
+            sq.run(c)
+
+    prepared = bm.PreparedBatch(pool, queries, outs, paths=[bm.PATH_DENSE] * len(queries))
 
     def batched():
-        bm.threshold_batch(pool, queries, outs, cards_batch, paths=[bm.PATH_DENSE] * len(queries))
+        prepared.run(cards_batch)
 
     def timed(fn):
         fn()  # warm-up (graph capture on first use)
@@ -255,10 +260,12 @@ def bench_selector(bm, datagen, n_train: int = 600, small: bool = False):
             best = min(best, e0.elapsed_time(e1) / 1e3)
         return best
 
-    t_plain = timed(lambda: [bm.query_run(pool, q, outs[i], cards_a[i:i + 1], path=bm.PATH_DENSE)
-                             for i, q in enumerate(test_q)])
+    singles = [bm.PreparedQuery(pool, q, outs[i], bm.PATH_DENSE) for i, q in enumerate(test_q)]
+    card_views = [cards_a[i:i + 1] for i in range(len(test_q))]
+    t_plain = timed(lambda: [sq.run(c) for sq, c in zip(singles, card_views)])
     chosen = []
-    t_sel = timed(lambda: chosen.append(bm.threshold_batch(pool, test_q, outs, cards_b)))
+    prepared = bm.PreparedBatch(pool, test_q, outs)  # PATH_AUTO: the installed selector routes
+    t_sel = timed(lambda: chosen.append(prepared.run(cards_b).copy()))
     same = bool(torch.equal(cards_a, cards_b))
     pool.status()
     pool.close()

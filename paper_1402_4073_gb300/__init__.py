@@ -261,25 +261,55 @@ def query_run(pool: Pool, query, out_words: torch.Tensor, out_card: torch.Tensor
     return int(chosen.value)
 
 
+class PreparedQuery:
+    """One query's bm_query struct, marshalled once: run() is then a single
+    bm_query_run call."""
+
+    def __init__(self, pool: Pool, query, out_words: torch.Tensor, path: int = PATH_AUTO):
+        if out_words.numel() * out_words.element_size() < 8 * pool.words:
+            raise ValueError("output buffer too small")
+        self.pool = pool
+        self.q, self._keep = _q_from(query, out_words, path)
+        self.ref = ctypes.byref(self.q)
+        self.chosen = ctypes.c_int32()
+
+    def run(self, out_card: torch.Tensor | None = None, stream=None) -> int:
+        check(lib.bm_query_run(self.pool.handle, self.ref, _dev_ptr(out_card, 8),
+                               ctypes.byref(self.chosen), _stream(stream)), "bm_query_run")
+        return int(self.chosen.value)
+
+
+class PreparedBatch:
+    """The bm_query array of a batch, marshalled once: run() is then a single
+    bm_threshold_batch call (re-runnable while queries and outputs stay)."""
+
+    def __init__(self, pool: Pool, queries, outs, paths=None):
+        nq = len(queries)
+        self.pool, self.nq = pool, nq
+        self.arr = (_native.bm_query * nq)()
+        self._keep = []
+        for i, qo in enumerate(queries):
+            if outs[i].numel() * outs[i].element_size() < 8 * pool.words:
+                raise ValueError("output buffer too small")
+            q, k = _q_from(qo, outs[i], None if paths is None else int(paths[i]))
+            self.arr[i] = q
+            self._keep.append(k)
+        self.chosen = np.zeros(nq, dtype=np.int32)
+
+    def run(self, out_cards: torch.Tensor, stream=None) -> np.ndarray:
+        if out_cards.numel() < self.nq:
+            raise ValueError("out_cards too small")
+        check(lib.bm_threshold_batch(self.pool.handle, self.arr, self.nq,
+                                     _dev_ptr(out_cards, 8 * self.nq), self.chosen.ctypes.data,
+                                     _stream(stream)), "bm_threshold_batch")
+        return self.chosen
+
+
 def threshold_batch(pool: Pool, queries, outs, out_cards: torch.Tensor, paths=None,
                     stream=None) -> np.ndarray:
     """Run a batch of queries (objects with ids, kind, theta, lo, hi, table)
     into outs[i]; cardinalities into out_cards[i].  Returns the chosen paths."""
-    nq = len(queries)
-    if out_cards.numel() < nq:
-        raise ValueError("out_cards too small")
-    arr = (_native.bm_query * nq)()
-    keep = []
-    for i, qo in enumerate(queries):
-        if outs[i].numel() * outs[i].element_size() < 8 * pool.words:
-            raise ValueError("output buffer too small")
-        q, k = _q_from(qo, outs[i], None if paths is None else int(paths[i]))
-        arr[i] = q
-        keep.append(k)
-    chosen = np.zeros(nq, dtype=np.int32)
-    check(lib.bm_threshold_batch(pool.handle, arr, nq, _dev_ptr(out_cards, 8 * nq),
-                                 chosen.ctypes.data, _stream(stream)), "bm_threshold_batch")
-    return chosen
+    return PreparedBatch(pool, queries, outs, paths).run(out_cards, stream).copy()
 
 
 def query_features(pool: Pool, query) -> np.ndarray:

@@ -23,7 +23,9 @@ namespace bm {
 
 constexpr int kBatchThreads = 256;        // dense: one 16-byte column per thread
 constexpr int kSparseBatchThreads = 512;
-constexpr uint32_t kSparseMaxTile = 65536;
+// Batched sparse items use tiles of at most 32768 rows, so that two sparse
+// CTAs (16-bit counters) fit on an SM whatever tile a query would take alone.
+constexpr uint32_t kSparseMaxTile = 32768;
 
 struct QueryDesc {
     const uint32_t* ids;
@@ -111,14 +113,48 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
     }
 }
 
-__global__ void __launch_bounds__(kSparseBatchThreads, 1)
+// One (query, row tile) item of ScanCount with BITS-bit counters.
+template <int BITS>
+__device__ __forceinline__ unsigned long long sparse_item(const QueryDesc* d, const Pred& pred,
+                                                          const uint32_t* tab, uint32_t* scratch,
+                                                          uint32_t* cnt, uint64_t tile,
+                                                          const BatchPoolArgs& pa) {
+    constexpr uint32_t kPer = 32 / BITS;
+    const uint32_t n = d->n, tile_rows = d->tile_rows;
+    for (uint32_t i = threadIdx.x; i < tile_rows / kPer; i += blockDim.x) cnt[i] = 0u;
+    __syncthreads();
+    const uint64_t rlo = tile * tile_rows;
+    const uint64_t rhi = min(rlo + tile_rows, pa.r_bits);
+    const uint32_t sub = tile_rows / kListTileRows;
+    const uint64_t t0 = tile * sub;
+    const uint64_t t1 = (t0 + sub < pa.tiles_per_list) ? t0 + sub : (uint64_t)pa.tiles_per_list;
+    count_tile<BITS, 4>(cnt, scratch, d->ids, n, pa.positions, pa.list_begin, pa.tile_index,
+                        pa.tiles_per_list, t0, t1, (uint32_t)rlo);
+    __syncthreads();
+    const uint32_t lanes = (uint32_t)((rhi - rlo + 31) / 32);
+    uint32_t* out32 = reinterpret_cast<uint32_t*>(d->out);
+    unsigned long long card = 0;
+    for (uint32_t l = threadIdx.x; l < lanes; l += blockDim.x) {
+        uint32_t o = counters_to_lane<BITS>(cnt + l * (32 / kPer), pred, tab);
+        const uint64_t row0 = rlo + 32ull * l;
+        if (row0 + 32 > pa.r_bits) o &= (1u << (pa.r_bits - row0)) - 1u;
+        out32[row0 / 32] = o;
+        card += __popc(o);
+    }
+    // the upper half of the last 64-bit word when r ends in its lower half
+    if (rhi == pa.r_bits && threadIdx.x == 0 && ((pa.r_bits + 31) / 32) % 2 == 1)
+        out32[(pa.r_bits + 31) / 32] = 0u;
+    return card;
+}
+
+__global__ void __launch_bounds__(kSparseBatchThreads, 2)
     sparse_batch_kernel(BatchHeader* h, BatchPoolArgs pa) {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ unsigned long long item_s;
     __shared__ unsigned long long part[kSparseBatchThreads / 32];
     uint32_t* tab = sm;                      // up to 2048 words (n <= 65535)
     uint32_t* scratch = sm + 2048;
-    uint32_t* cnt = scratch + ((kScanSmemWords + 3) & ~3u);  // 16-bit counters, two per word
+    uint32_t* cnt = scratch + ((kScanSmemWords + 3) & ~3u);  // counters
     const uint32_t ns = h->n_sparse;
     const uint64_t total = ns ? h->sparse_off[ns] : 0;
     for (;;) {
@@ -138,7 +174,7 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 1)
         }
         const uint32_t qi = h->sparse_list[lo];
         const QueryDesc* d = h->desc + qi;
-        const uint32_t n = d->n, tile_rows = d->tile_rows;
+        const uint32_t n = d->n;
         const uint64_t tile = item - h->sparse_off[lo];
         const Pred pred = d->pred;
         // truth table of f over 0..n
@@ -161,36 +197,18 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 1)
             }
             tab[w] = bits;
         }
-        for (uint32_t i = threadIdx.x; i < tile_rows / 2; i += blockDim.x) cnt[i] = 0u;
-        __syncthreads();
-        const uint64_t rlo = tile * tile_rows;
-        const uint64_t rhi = min(rlo + tile_rows, pa.r_bits);
-        const uint32_t sub = tile_rows / kListTileRows;
-        const uint64_t t0 = tile * sub;
-        const uint64_t t1 = (t0 + sub < pa.tiles_per_list) ? t0 + sub : (uint64_t)pa.tiles_per_list;
-        count_tile<16, 4>(cnt, scratch, d->ids, n, pa.positions, pa.list_begin, pa.tile_index,
-                       pa.tiles_per_list, t0, t1, (uint32_t)rlo);
-        __syncthreads();
-        const uint32_t lanes = (uint32_t)((rhi - rlo + 31) / 32);
-        uint32_t* out32 = reinterpret_cast<uint32_t*>(d->out);
-        unsigned long long card = 0;
-        for (uint32_t l = threadIdx.x; l < lanes; l += blockDim.x) {
-            uint32_t o = counters_to_lane<16>(cnt + l * 16, pred, tab);
-            const uint64_t row0 = rlo + 32ull * l;
-            if (row0 + 32 > pa.r_bits) o &= (1u << (pa.r_bits - row0)) - 1u;
-            out32[row0 / 32] = o;
-            card += __popc(o);
-        }
-        // the upper half of the last 64-bit word when r ends in its lower half
-        if (rhi == pa.r_bits && threadIdx.x == 0 && ((pa.r_bits + 31) / 32) % 2 == 1)
-            out32[(pa.r_bits + 31) / 32] = 0u;
+        // 8-bit counters hold every count when n <= 255 (the counter-width switch by N)
+        const unsigned long long card =
+            n <= 255 ? sparse_item<8>(d, pred, tab, scratch, cnt, tile, pa)
+                     : sparse_item<16>(d, pred, tab, scratch, cnt, tile, pa);
         block_card_add(card, reinterpret_cast<unsigned long long*>(h->out_cards + qi), part);
         __syncthreads();
     }
 }
 
-size_t sparse_batch_smem() {
-    return (2048 + (((size_t)kScanSmemWords + 3) & ~(size_t)3) + (size_t)kSparseMaxTile / 2) * 4;
+// Shared memory of the sparse batch kernel for tiles of up to max_tile rows.
+size_t sparse_batch_smem(uint32_t max_tile) {
+    return (2048 + (((size_t)kScanSmemWords + 3) & ~(size_t)3) + (size_t)max_tile / 2) * 4;
 }
 
 }  // namespace
@@ -210,7 +228,8 @@ struct BatchState {
     static constexpr int kSlots = 4;
     BatchSlot slots[kSlots];
     int next = 0;
-    cudaStream_t capture = nullptr;
+    cudaStream_t capture = nullptr, capture2 = nullptr;  // fork/join capture of the graph
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaStream_t infer = nullptr;
     float* d_sel = nullptr;  // selector inference buffers
     size_t sel_cap = 0;
@@ -227,6 +246,9 @@ void batch_state_free(bm_pool* p) {
         if (sl.d) cudaFree(sl.d);
     }
     if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->capture2) cudaStreamDestroy(b->capture2);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
     if (b->infer) cudaStreamDestroy(b->infer);
     if (b->d_sel) cudaFree(b->d_sel);
     delete b;
@@ -269,25 +291,40 @@ static int slot_reserve(bm_pool* p, BatchSlot& sl, size_t bytes) {
     return BM_OK;
 }
 
-static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, const BatchPoolArgs& pa,
-                     cudaGraphExec_t* out) {
+static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, uint32_t max_tile,
+                     const BatchPoolArgs& pa, cudaGraphExec_t* out) {
     const int adder = b->cfg.adder, L = b->cfg.words_per_thread == 1 ? 2 : 4;
-    const int key = K * 64 + adder * 8 + L;
+    const int tile_code = max_tile <= 16384 ? 0 : max_tile <= 32768 ? 1 : 2;
+    const uint32_t tile_cap = 16384u << tile_code;
+    const int key = ((K * 64 + adder * 8 + L) << 2) | tile_code;
     auto it = sl.graphs.find(key);
     if (it != sl.graphs.end()) {
         *out = it->second;
         return BM_OK;
     }
-    if (!b->capture) BM_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
+    if (!b->capture) {
+        BM_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
+        BM_CUDA_TRY(cudaStreamCreateWithFlags(&b->capture2, cudaStreamNonBlocking));
+        BM_CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        BM_CUDA_TRY(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
+    }
     BatchHeader* h = static_cast<BatchHeader*>(sl.d);
+    const size_t sp_smem = sparse_batch_smem(tile_cap);
+    int optin = 0;
+    BM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
     const unsigned dense_grid = (unsigned)(p->sm_count * std::max(1, b->cfg.ctas_per_sm));
-    const unsigned sparse_grid = (unsigned)p->sm_count;
+    const unsigned sparse_grid =
+        (unsigned)p->sm_count * (2 * sp_smem + 2048 <= (size_t)optin ? 2u : 1u);
     auto dense_fn = [&](auto fn) -> int {
+        // the dense and the sparse persistent kernels run side by side
         BM_CUDA_TRY(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
         batch_zero_kernel<<<1, 256, 0, b->capture>>>(h);
+        BM_CUDA_TRY(cudaEventRecord(b->fork, b->capture));
+        BM_CUDA_TRY(cudaStreamWaitEvent(b->capture2, b->fork, 0));
         fn<<<dense_grid, kBatchThreads, 0, b->capture>>>(h, pa);
-        sparse_batch_kernel<<<sparse_grid, kSparseBatchThreads, sparse_batch_smem(), b->capture>>>(
-            h, pa);
+        sparse_batch_kernel<<<sparse_grid, kSparseBatchThreads, sp_smem, b->capture2>>>(h, pa);
+        BM_CUDA_TRY(cudaEventRecord(b->join, b->capture2));
+        BM_CUDA_TRY(cudaStreamWaitEvent(b->capture, b->join, 0));
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(b->capture, &g);
         if (e != cudaSuccess) {
@@ -307,7 +344,7 @@ static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, const Batc
     };
     BM_CUDA_TRY(cudaFuncSetAttribute(sparse_batch_kernel,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sparse_batch_smem()));
+                                     (int)sparse_batch_smem(kSparseMaxTile)));
 #define BM_BATCH_DISPATCH(LL)                                                      \
     if (adder == 2 && LL == 4) {                                                   \
         if (K <= 5) return dense_fn(dense_batch_kernel<5, 16, 4>);                 \
@@ -439,11 +476,13 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
     std::vector<Pred> preds(nq);
     std::vector<uint32_t> dense_list, sparse_list;
     std::vector<uint64_t> sparse_off(1, 0);
+    uint32_t max_tile = 0;
     for (uint32_t i = 0; i < nq; ++i) {
         preds[i] = compile_pred(truth[i].data(), q[i].n);
         if (preds[i].mode == 2) total_tab += preds[i].table_words32;
         if (cand[i].path == BM_PATH_SPARSE) {
             if (cand[i].tile_rows > kSparseMaxTile) cand[i].tile_rows = kSparseMaxTile;
+            max_tile = std::max(max_tile, cand[i].tile_rows);
             sparse_list.push_back(i);
             sparse_off.push_back(sparse_off.back() +
                                  (p->r_bits + cand[i].tile_rows - 1) / cand[i].tile_rows);
@@ -522,7 +561,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
     const int K = planes_for(max_dense_n);
     const int kk = K <= 5 ? 5 : K <= 9 ? 9 : K <= 11 ? 11 : K <= 13 ? 13 : 17;
     cudaGraphExec_t ex = nullptr;
-    rc = graph_for(p, b, sl, kk, pa, &ex);
+    rc = graph_for(p, b, sl, kk, max_tile, pa, &ex);
     if (rc) return rc;
     BM_CUDA_TRY(cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, s));
     BM_CUDA_TRY(cudaGraphLaunch(ex, s));
