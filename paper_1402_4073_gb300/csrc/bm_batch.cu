@@ -26,6 +26,9 @@ constexpr int kSparseBatchThreads = 512;
 // Batched sparse items use tiles of at most 32768 rows, so that two sparse
 // CTAs (16-bit counters) fit on an SM whatever tile a query would take alone.
 constexpr uint32_t kSparseMaxTile = 32768;
+// Pieces a warp has in flight in batched ScanCount items (the most that fit
+// in the 64 registers two 512-thread CTAs per SM leave).
+constexpr int kSparseBatchUnroll = 3;
 
 struct QueryDesc {
     const uint32_t* ids;
@@ -117,19 +120,20 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
 template <int BITS>
 __device__ __forceinline__ unsigned long long sparse_item(const QueryDesc* d, const Pred& pred,
                                                           const uint32_t* tab, uint32_t* scratch,
-                                                          uint32_t* cnt, uint64_t tile,
-                                                          const BatchPoolArgs& pa) {
+                                                          uint32_t* cnt, uint32_t cnt_words,
+                                                          uint64_t tile, const BatchPoolArgs& pa) {
     constexpr uint32_t kPer = 32 / BITS;
     const uint32_t n = d->n, tile_rows = d->tile_rows;
-    for (uint32_t i = threadIdx.x; i < tile_rows / kPer; i += blockDim.x) cnt[i] = 0u;
-    __syncthreads();
     const uint64_t rlo = tile * tile_rows;
     const uint64_t rhi = min(rlo + tile_rows, pa.r_bits);
     const uint32_t sub = tile_rows / kListTileRows;
     const uint64_t t0 = tile * sub;
     const uint64_t t1 = (t0 + sub < pa.tiles_per_list) ? t0 + sub : (uint64_t)pa.tiles_per_list;
-    count_tile<BITS, 4>(cnt, scratch, d->ids, n, pa.positions, pa.list_begin, pa.tile_index,
-                        pa.tiles_per_list, t0, t1, (uint32_t)rlo);
+    count_tile<BITS, kSparseBatchUnroll>(cnt, scratch, d->ids, n,
+                                         reinterpret_cast<const uint4*>(pa.positions),
+                                         pa.list_begin, pa.tile_index, pa.tiles_per_list, t0, t1,
+                                         (uint32_t)rlo, (uint32_t)(rhi - rlo),
+                                         cnt_words * kPer);  // spares past every item's counters
     __syncthreads();
     const uint32_t lanes = (uint32_t)((rhi - rlo + 31) / 32);
     uint32_t* out32 = reinterpret_cast<uint32_t*>(d->out);
@@ -157,6 +161,11 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 2)
     uint32_t* cnt = scratch + ((kScanSmemWords + 3) & ~3u);  // counters
     const uint32_t ns = h->n_sparse;
     const uint64_t total = ns ? h->sparse_off[ns] : 0;
+    // counters start at zero; evaluating an item clears the ones it used.  The
+    // launch sized the counters for its largest tile: zero what it allocated.
+    const uint32_t cnt_words =
+        dynamic_smem_bytes() / 4 - 2048 - ((kScanSmemWords + 3) & ~3u) - 32;
+    for (uint32_t i = threadIdx.x; i < cnt_words; i += blockDim.x) cnt[i] = 0u;
     for (;;) {
         if (threadIdx.x == 0) item_s = atomicAdd(&h->sparse_next, 1ull);
         __syncthreads();
@@ -176,9 +185,10 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 2)
         const QueryDesc* d = h->desc + qi;
         const uint32_t n = d->n;
         const uint64_t tile = item - h->sparse_off[lo];
-        const Pred pred = d->pred;
-        // truth table of f over 0..n
-        const uint32_t tab_words = (n + 1 + 31) / 32;
+        const Pred& pred = d->pred;  // read in place: no registers held across the count
+        // truth table of f over 0..n (a plain threshold is compared directly)
+        const bool plain = pred.mode == 1 && pred.ntrans == 1 && pred.v0 == 0;
+        const uint32_t tab_words = plain ? 0u : (n + 1 + 31) / 32;
         for (uint32_t w = threadIdx.x; w < tab_words; w += blockDim.x) {
             uint32_t bits = 0;
             if (pred.mode == 2) {
@@ -199,8 +209,8 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 2)
         }
         // 8-bit counters hold every count when n <= 255 (the counter-width switch by N)
         const unsigned long long card =
-            n <= 255 ? sparse_item<8>(d, pred, tab, scratch, cnt, tile, pa)
-                     : sparse_item<16>(d, pred, tab, scratch, cnt, tile, pa);
+            n <= 255 ? sparse_item<8>(d, pred, tab, scratch, cnt, cnt_words, tile, pa)
+                     : sparse_item<16>(d, pred, tab, scratch, cnt, cnt_words, tile, pa);
         block_card_add(card, reinterpret_cast<unsigned long long*>(h->out_cards + qi), part);
         __syncthreads();
     }
@@ -208,7 +218,8 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 2)
 
 // Shared memory of the sparse batch kernel for tiles of up to max_tile rows.
 size_t sparse_batch_smem(uint32_t max_tile) {
-    return (2048 + (((size_t)kScanSmemWords + 3) & ~(size_t)3) + (size_t)max_tile / 2) * 4;
+    // truth table, scratch, 16-bit counters and one spare word per lane
+    return (2048 + (((size_t)kScanSmemWords + 3) & ~(size_t)3) + (size_t)max_tile / 2 + 32) * 4;
 }
 
 }  // namespace

@@ -182,6 +182,13 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
+// Bytes of dynamic shared memory this launch was given.
+__device__ __forceinline__ uint32_t dynamic_smem_bytes() {
+    uint32_t r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
 // Streaming 128-bit load that bypasses L1 allocation.
 __device__ __forceinline__ uint4 ld_stream(const void* p) {
     uint4 v;

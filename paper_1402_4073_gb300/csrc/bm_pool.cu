@@ -134,6 +134,26 @@ __global__ void wait_selftest_kernel(int* err, unsigned long long limit_ns) {
     }
 }
 
+// Copy list j (src[src_off[j] .. src_off[j+1])) to dst + dst_off[j], a
+// multiple of four entries, and fill its padding up to the next multiple of
+// four with a value that no row tile holding the list's last position can
+// contain (tiles are aligned and at most 65536 rows): all ones when the last
+// position is below 65536, else 0.  A 16-byte vector read anywhere inside the
+// padded list then holds only positions of that list or such padding.
+__global__ void place_lists_kernel(const uint32_t* src, const uint64_t* src_off, uint32_t* dst,
+                                   const uint64_t* dst_off, uint32_t count) {
+    for (uint32_t j = blockIdx.x; j < count; j += gridDim.x) {
+        const uint64_t s0 = src_off[j], len = src_off[j + 1] - s0;
+        uint32_t* d = dst + dst_off[j];
+        for (uint64_t i = threadIdx.x; i < len; i += blockDim.x) d[i] = src[s0 + i];
+        const uint32_t pad = (uint32_t)((4 - (len & 3)) & 3);
+        if (len && threadIdx.x < pad) {
+            const uint32_t last = src[s0 + len - 1];
+            d[len + threadIdx.x] = last < 65536u ? 0xFFFFFFFFu : 0u;
+        }
+    }
+}
+
 // Strict increase and range check of device-resident lists; sets *bad.
 __global__ void list_check_kernel(const uint32_t* pos, uint64_t len, uint64_t r_bits, int* bad) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
@@ -259,8 +279,18 @@ int bm_pool_put_positions(bm_pool* p, uint32_t first_id, uint32_t count, const u
         if (offsets[j + 1] < offsets[j]) return BM_EINVAL;
     if (total && !positions) return BM_EINVAL;
     if (total > 0xFFFFFFFFull) return BM_EINVAL;  // tile index entries are 32-bit
+    // every list starts on a 16-byte boundary and is padded to a multiple of
+    // four entries (the sparse kernels read whole 16-byte vectors)
+    std::vector<uint64_t> src_off(count + 1), dst_off(count);
+    uint64_t padded = 0;
+    for (uint32_t j = 0; j < count; ++j) {
+        src_off[j] = offsets[j] - offsets[0];
+        dst_off[j] = p->pos_used + padded;
+        padded += (offsets[j + 1] - offsets[j] + 3) & ~3ull;
+    }
+    src_off[count] = total;
     // kernels address the arena with 32-bit entry offsets
-    if (p->pos_used + total > 0xFFFFFFFFull) return BM_ENOMEM;
+    if (p->pos_used + padded > 0xFFFFFFFCull) return BM_ENOMEM;
     std::lock_guard<std::mutex> lk(p->mu);
     BM_CUDA_TRY(cudaSetDevice(p->device));
     if (!on_device) {
@@ -271,9 +301,10 @@ int bm_pool_put_positions(bm_pool* p, uint32_t first_id, uint32_t count, const u
                     return BM_ERANGE;
     }
     // grow the arena (lists are appended; a replaced list's old space is not reused)
-    if (p->pos_used + total > p->pos_cap) {
-        uint64_t cap = std::max<uint64_t>(p->pos_used + total, p->pos_cap + p->pos_cap / 2);
+    if (p->pos_used + padded > p->pos_cap) {
+        uint64_t cap = std::max<uint64_t>(p->pos_used + padded, p->pos_cap + p->pos_cap / 2);
         cap = std::max<uint64_t>(cap, 1 << 20);
+        cap = std::min<uint64_t>(cap, 0x100000000ull);
         uint32_t* nd = nullptr;
         int rc = track_alloc(p, (void**)&nd, cap * 4);
         if (rc) return rc;
@@ -291,10 +322,42 @@ int bm_pool_put_positions(bm_pool* p, uint32_t first_id, uint32_t count, const u
         BM_CUDA_TRY(cudaMemset(p->d_tile_index, 0, (size_t)p->capacity * (p->tiles_per_list + 1) * 4));
         BM_CUDA_TRY(cudaMemset(p->d_list_begin, 0, (size_t)p->capacity * 8));
     }
-    uint32_t* dst = p->d_pos + p->pos_used;
-    if (total)
-        BM_CUDA_TRY(cudaMemcpy(dst, positions + offsets[0], total * 4,
-                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    if (total) {
+        // source lists on the device (the caller's, or a temporary copy of
+        // the host's), then one placing launch into the arena
+        const uint32_t* src = positions + offsets[0];
+        uint32_t* tmp = nullptr;
+        uint64_t* d_off = nullptr;
+        const size_t off_bytes = (size_t)(2 * count + 1) * 8;
+        int rc = track_alloc(p, (void**)&d_off, off_bytes);
+        if (!rc && !on_device) rc = track_alloc(p, (void**)&tmp, total * 4);
+        if (rc) {
+            track_free(p, d_off, off_bytes);
+            return rc;
+        }
+        cudaError_t e = cudaSuccess;
+        if (!on_device) {
+            e = cudaMemcpy(tmp, src, total * 4, cudaMemcpyHostToDevice);
+            src = tmp;
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d_off, src_off.data(), (size_t)(count + 1) * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d_off + count + 1, dst_off.data(), (size_t)count * 8,
+                           cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            place_lists_kernel<<<std::min<uint32_t>(count, 65535u), 256>>>(src, d_off, p->d_pos,
+                                                                          d_off + count + 1, count);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        track_free(p, tmp, total * 4);
+        track_free(p, d_off, off_bytes);
+        if (e != cudaSuccess) {
+            bm_note_cuda_error(e, "put_positions placement", __FILE__, __LINE__);
+            return BM_ECUDA;
+        }
+    }
     if (on_device) {
         int* d_bad = nullptr;
         int rc = track_alloc(p, (void**)&d_bad, sizeof(int));
@@ -304,8 +367,8 @@ int bm_pool_put_positions(bm_pool* p, uint32_t first_id, uint32_t count, const u
             uint64_t len = offsets[j + 1] - offsets[j];
             if (!len) continue;
             uint64_t blocks = std::min<uint64_t>((len + 255) / 256, 4096);
-            list_check_kernel<<<(unsigned)blocks, 256>>>(dst + (offsets[j] - offsets[0]), len,
-                                                         p->r_bits, d_bad);
+            list_check_kernel<<<(unsigned)blocks, 256>>>(p->d_pos + dst_off[j], len, p->r_bits,
+                                                         d_bad);
         }
         int bad = 0;
         cudaError_t e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
@@ -313,11 +376,9 @@ int bm_pool_put_positions(bm_pool* p, uint32_t first_id, uint32_t count, const u
         if (e != cudaSuccess) return BM_ECUDA;
         if (bad) return BM_ERANGE;
     }
-    std::vector<uint64_t> begins(count);
     for (uint32_t j = 0; j < count; ++j) {
         const uint64_t len = offsets[j + 1] - offsets[j];
-        const uint64_t b = p->pos_used + (offsets[j] - offsets[0]);
-        begins[j] = b;
+        const uint64_t b = dst_off[j];
         uint32_t* idx = p->d_tile_index + (uint64_t)(first_id + j) * (p->tiles_per_list + 1);
         list_index_kernel<<<(p->tiles_per_list + 1 + 255) / 256, 256>>>(p->d_pos + b, len,
                                                                         p->tiles_per_list, idx);
@@ -327,10 +388,10 @@ int bm_pool_put_positions(bm_pool* p, uint32_t first_id, uint32_t count, const u
         p->list_present[first_id + j] = 1;
         if (!p->dense_present[first_id + j]) p->card[first_id + j] = len;
     }
-    BM_CUDA_TRY(cudaMemcpy(p->d_list_begin + first_id, begins.data(), (size_t)count * 8,
+    BM_CUDA_TRY(cudaMemcpy(p->d_list_begin + first_id, dst_off.data(), (size_t)count * 8,
                            cudaMemcpyHostToDevice));
     BM_CUDA_TRY(cudaDeviceSynchronize());
-    p->pos_used += total;
+    p->pos_used += padded;
     return BM_OK;
 }
 

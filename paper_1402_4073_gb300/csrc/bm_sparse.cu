@@ -7,10 +7,11 @@
 // width switch by N, packed four or two to a 32-bit word and incremented
 // with shared-memory atomics).  The tile's slice of a list comes from the
 // pool's per-list tile index (first entry at every multiple of 8192 rows), so
-// a list is never searched; the slices of up to 1024 lists are concatenated
-// and walked by all threads at once (bm_scan_common.cuh).  Then each thread
-// turns 32 counters into one 32-bit output lane through the truth table of f
-// held in shared memory, stores it and popcounts it.
+// a list is never searched; the slices of up to 1024 lists are laid end to
+// end as one stream of 16-byte vectors and read by all lanes at once
+// (bm_scan_common.cuh).  Then each thread turns 32 counters into one 32-bit
+// output lane through the truth table of f held in shared memory, stores it
+// and popcounts it.
 #include <algorithm>
 
 #include "bm_scan_common.cuh"
@@ -32,7 +33,9 @@ __device__ void build_truth(const Pred& pr, uint32_t n, uint32_t* tab, uint32_t 
                 if (c > n) break;
                 uint32_t v = pr.v0;
                 if (pr.mode == 1)
-                    for (uint32_t i = 0; i < pr.ntrans; ++i) v ^= (c >= pr.trans[i]) ? 1u : 0u;
+#pragma unroll
+                    for (int i = 0; i < kMaxTransitions; ++i)
+                        if ((uint32_t)i < pr.ntrans) v ^= (c >= pr.trans[i]) ? 1u : 0u;
                 bits |= v << b;
             }
         }
@@ -40,8 +43,10 @@ __device__ void build_truth(const Pred& pr, uint32_t n, uint32_t* tab, uint32_t 
     }
 }
 
-template <int BITS, int U>  // counter width: 8 or 16; slices in flight per warp
-__global__ void __launch_bounds__(512, 3) scancount_kernel(SparseArgs a) {
+// Three CTAs of 8-bit counters fit on an SM at 32768-row tiles; eight pieces
+// in flight need more than the 40 registers that three 512-thread CTAs leave.
+template <int BITS, int U>  // counter width: 8 or 16; pieces in flight per warp
+__global__ void __launch_bounds__(512, (BITS == 8 && U <= 4) ? 3 : 2) scancount_kernel(SparseArgs a) {
     extern __shared__ __align__(16) uint32_t sm[];
     constexpr uint32_t kPer = 32 / BITS;  // counters per 32-bit word
     const uint32_t tab_words = (a.n + 1 + 31) / 32;
@@ -55,15 +60,17 @@ __global__ void __launch_bounds__(512, 3) scancount_kernel(SparseArgs a) {
     const uint64_t ntiles = (a.r_bits + a.tile_rows - 1) / a.tile_rows;
     const uint32_t sub = a.tile_rows / kListTileRows;  // index entries per tile
     unsigned long long card = 0;
+    // counters start at zero; evaluating a tile clears them for the next one
+    for (uint32_t i = threadIdx.x; i < cnt_words; i += blockDim.x) cnt[i] = 0u;
+    __syncthreads();
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint64_t lo = tile * a.tile_rows;
         const uint64_t hi = min(lo + a.tile_rows, a.r_bits);
-        for (uint32_t i = threadIdx.x; i < cnt_words; i += blockDim.x) cnt[i] = 0u;
-        __syncthreads();
         const uint64_t t0 = tile * sub;
         const uint64_t t1 = (t0 + sub < a.tiles_per_list) ? t0 + sub : (uint64_t)a.tiles_per_list;
-        count_tile<BITS, U>(cnt, scratch, a.ids, a.n, a.positions, a.list_begin, a.tile_index,
-                         a.tiles_per_list, t0, t1, (uint32_t)lo);
+        count_tile<BITS, U>(cnt, scratch, a.ids, a.n, reinterpret_cast<const uint4*>(a.positions),
+                            a.list_begin, a.tile_index, a.tiles_per_list, t0, t1, (uint32_t)lo,
+                            (uint32_t)(hi - lo), a.tile_rows);
         __syncthreads();
         // 32 rows per thread -> one 32-bit output lane
         const uint32_t lanes = (uint32_t)((hi - lo + 31) / 32);
@@ -89,11 +96,13 @@ __global__ void __launch_bounds__(512, 3) scancount_kernel(SparseArgs a) {
 
 int launch_sparse(const SparseArgs& a, const SparseConfig& cfg, int sm_count, cudaStream_t s) {
     if (a.r_bits == 0) return BM_OK;
-    if (a.tile_rows == 0 || a.tile_rows % kListTileRows) return BM_EINVAL;
+    // padded lists keep their padding out of every tile of at most 65536 rows
+    if (a.tile_rows == 0 || a.tile_rows % kListTileRows || a.tile_rows > 65536) return BM_EINVAL;
     const int bits = a.n <= 255 ? 8 : 16;
     const size_t tab_words = ((size_t)(a.n + 1 + 31) / 32 + 3) & ~(size_t)3;
     const size_t scratch_words = ((size_t)dev::kScanSmemWords + 3) & ~(size_t)3;
-    const size_t smem = (tab_words + scratch_words + (size_t)a.tile_rows * bits / 32) * 4;
+    // counters, then one spare word per lane
+    const size_t smem = (tab_words + scratch_words + (size_t)a.tile_rows * bits / 32 + 32) * 4;
     const uint64_t ntiles = (a.r_bits + a.tile_rows - 1) / a.tile_rows;
     const int threads = std::max(64, std::min(512, cfg.threads));
     const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);

@@ -91,6 +91,33 @@ def test_batch_equals_alone_and_repeats(bm, dg, mixed):
                 assert int(c[j].item()) == cards[k * 20 + j]
 
 
+@pytest.mark.parametrize("tile", [8192, 16384, 32768, 65536])
+def test_batch_sparse_counter_widths_interleaved(bm, oracle_lib, dg, tile):
+    """One batch of ScanCount items with 8-bit (n <= 255) and 16-bit (n > 255)
+    counters interleaved, so CTAs go from one width to the other: counters
+    and spare words left by one item never leak into the next.  Run twice."""
+    r_bits = (1 << 18) + 77
+    n_bm = 1300
+    d = dg.pool_densities(dg.STREAM_TESTS + 12200, n_bm, 1e-4, 2e-2)
+    words = dg.bernoulli(dg.STREAM_TESTS + 12201, r_bits, d)
+    words[:, 7] |= np.uint64(0xFF00)  # rows where every input is set
+    flat, offs = dg.positions(words, r_bits)
+    small = dg._queries(dg.STREAM_TESTS + 12202, 20, n_bm, 2, 255, 40, 0.2)
+    large = dg._queries(dg.STREAM_TESTS + 12203, 20, n_bm, 256, n_bm, 300, 0.2)
+    queries = [q for pair in zip(small, large) for q in pair]
+    with bm.Pool(r_bits, n_bm) as pool:
+        pool.put_dense(words)
+        pool.put_positions(flat, offs)
+        pool.set_sparse_config(tile, 512, 2)
+        want = [oracle_lib.query(words, q, r_bits) for q in queries]
+        for rep in range(2):
+            outs, cards, chosen = _batch(bm, pool, queries, [bm.PATH_SPARSE] * len(queries))
+            assert all(c == bm.PATH_SPARSE for c in chosen)
+            for i, q in enumerate(queries):
+                assert np.array_equal(outs[i], want[i][0]), f"rep {rep} query {i} (n={q.n})"
+                assert cards[i] == want[i][1], f"rep {rep} query {i} card"
+
+
 def test_batch_single_query_and_errors(bm, oracle_lib, dg):
     r_bits = 70000
     words = dg.bernoulli(dg.STREAM_TESTS + 12100, r_bits, np.full(10, 0.3))

@@ -106,6 +106,70 @@ def test_sparse_workload_subset(bm, oracle_lib, dg):
                 assert chosen in (bm.PATH_DENSE, bm.PATH_SPARSE)
 
 
+def _lists_to_words(lists, r_bits):
+    words = np.zeros((len(lists), (r_bits + 63) // 64), dtype=np.uint64)
+    for k, l in enumerate(lists):
+        for x in l:
+            words[k, x // 64] |= np.uint64(1) << np.uint64(x % 64)
+    return words
+
+
+def _flat(lists):
+    offs = np.zeros(len(lists) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([len(l) for l in lists])
+    flat = np.concatenate([np.asarray(l, dtype=np.uint32) for l in lists]) if offs[-1] else \
+        np.zeros(0, np.uint32)
+    return flat, offs
+
+
+@pytest.mark.parametrize("tile", [8192, 16384, 32768, 65536])
+def test_list_padding_and_alignment(bm, oracle_lib, dg, tile):
+    """Lists of every length mod 4, last positions just below and above 65536,
+    slices that cross tile and index boundaries, an empty list, the last row;
+    loaded in several calls (host and device, one list replaced): the pool's
+    16-byte alignment and padding never add or drop a count."""
+    r_bits = 3 * 65536 + 5000
+    rng = dg.uniform(dg.STREAM_TESTS + 11050, 4000)
+    rand = np.unique((rng * r_bits).astype(np.uint64)).astype(np.uint32)
+    lists = [
+        [65535],
+        [65536],
+        [0, 1, 2, 3, 4],
+        [65533, 65534, 65535, 65536, 65537, 65538],
+        [],
+        [r_bits - 1],
+        list(rand[: 4 * (len(rand) // 4) - 1]),
+        [8191, 8192, 16383, 16384, 32767, 32768],
+        [65532, 65533, 65534],
+        [131071, 131072, 131073],
+    ]
+    replaced = [7, 65535, 65536, 131072, r_bits - 2]
+    with bm.Pool(r_bits, len(lists)) as pool:
+        f0, o0 = _flat(lists[:4])
+        pool.put_positions(f0, o0)
+        f1, o1 = _flat(lists[4:8])
+        pool.put_positions(torch.from_numpy(f1.view(np.int32).copy()).cuda(), o1, first_id=4)
+        f2, o2 = _flat(lists[8:])
+        pool.put_positions(f2, o2, first_id=8)
+        f3, o3 = _flat([replaced])
+        pool.put_positions(f3, o3, first_id=2)  # appended; the old copy stays unused
+        lists[2] = replaced
+        flat, offs = _flat(lists)
+        words = _lists_to_words(lists, r_bits)
+        pool.put_dense(words)
+        pool.set_sparse_config(tile, 512, 2)
+        ids = np.array(list(range(len(lists))) + [0, 3, 3, 9], dtype=np.uint32)
+        for theta in (1, 2, 3, 4):
+            q = dg.Query(ids, 0, theta=theta)
+            got, _ = _run(bm, pool, q, bm.PATH_SPARSE)
+            _eq(got, oracle_lib.scancount(flat, offs, ids, r_bits, theta), f"theta={theta}")
+            _eq(got, oracle_lib.query(words, q, r_bits), f"dense view theta={theta}")
+        for k in range(len(lists)):  # each list alone reproduces its bitmap
+            q = dg.Query(np.array([k]), 0, theta=1)
+            got, _ = _run(bm, pool, q, bm.PATH_SPARSE)
+            assert np.array_equal(got[0], words[k]) and got[1] == len(lists[k]), k
+
+
 def test_lists_from_device_and_validation(bm, dg):
     r_bits = 50000
     words = dg.bernoulli(dg.STREAM_TESTS + 11300, r_bits, np.array([0.01, 0.02, 0.03]))
