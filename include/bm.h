@@ -158,8 +158,9 @@ int bm_pool_get_dense_config(bm_pool* pool, bm_dense_config_t* cfg);
 /*
  * Shape of the sparse (ScanCount) kernel: tile_rows rows of counters per CTA
  * (a multiple of 8192, at most 65536), `threads` per CTA (64..512, a
- * multiple of 32), ctas_per_sm (1..8), unroll = list slices each warp keeps
- * in flight (4 or 8).  BM_EINVAL outside these ranges.
+ * multiple of 32), ctas_per_sm (1..8), unroll = 32-vector pieces in each
+ * of the two load batches a warp keeps in flight (2 or 4).  BM_EINVAL
+ * outside these ranges.
  */
 typedef struct bm_sparse_config_t {
     uint32_t tile_rows;

@@ -173,7 +173,7 @@ int bm_pool_set_sparse_config(bm_pool* p, const bm_sparse_config_t* c) {
     if (!p || !c || c->tile_rows == 0 || c->tile_rows % kListTileRows || c->tile_rows > 65536)
         return BM_EINVAL;
     if (c->threads < 64 || c->threads > 512 || c->threads % 32 || c->ctas_per_sm < 1 ||
-        c->ctas_per_sm > 8 || (c->unroll != 4 && c->unroll != 8))
+        c->ctas_per_sm > 8 || (c->unroll != 2 && c->unroll != 4))
         return BM_EINVAL;
     std::lock_guard<std::mutex> lk(p->mu);
     p->sparse_cfg = SparseConfig{c->tile_rows, c->threads, c->ctas_per_sm, c->unroll};

@@ -26,9 +26,9 @@ constexpr int kSparseBatchThreads = 512;
 // Batched sparse items use tiles of at most 32768 rows, so that two sparse
 // CTAs (16-bit counters) fit on an SM whatever tile a query would take alone.
 constexpr uint32_t kSparseMaxTile = 32768;
-// Pieces a warp has in flight in batched ScanCount items (the most that fit
-// in the 64 registers two 512-thread CTAs per SM leave).
-constexpr int kSparseBatchUnroll = 3;
+// Pieces per load batch of a warp in batched ScanCount items (two batches
+// in flight; they fit in the 64 registers two 512-thread CTAs per SM leave).
+constexpr int kSparseBatchUnroll = 2;
 
 struct QueryDesc {
     const uint32_t* ids;
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
 template <int BITS>
 __device__ __forceinline__ unsigned long long sparse_item(const QueryDesc* d, const Pred& pred,
                                                           const uint32_t* tab, uint32_t* scratch,
+                                                          uint32_t* s_next,
                                                           uint32_t* cnt, uint32_t cnt_words,
                                                           uint64_t tile, const BatchPoolArgs& pa) {
     constexpr uint32_t kPer = 32 / BITS;
@@ -129,7 +130,7 @@ __device__ __forceinline__ unsigned long long sparse_item(const QueryDesc* d, co
     const uint32_t sub = tile_rows / kListTileRows;
     const uint64_t t0 = tile * sub;
     const uint64_t t1 = (t0 + sub < pa.tiles_per_list) ? t0 + sub : (uint64_t)pa.tiles_per_list;
-    count_tile<BITS, kSparseBatchUnroll>(cnt, scratch, d->ids, n,
+    count_tile<BITS, kSparseBatchUnroll>(cnt, scratch, s_next, d->ids, n,
                                          reinterpret_cast<const uint4*>(pa.positions),
                                          pa.list_begin, pa.tile_index, pa.tiles_per_list, t0, t1,
                                          (uint32_t)rlo, (uint32_t)(rhi - rlo),
@@ -157,14 +158,15 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 2)
     __shared__ unsigned long long item_s;
     __shared__ unsigned long long part[kSparseBatchThreads / 32];
     uint32_t* tab = sm;                      // up to 2048 words (n <= 65535)
+    __shared__ uint32_t s_next;  // next group of lists to count
     uint32_t* scratch = sm + 2048;
-    uint32_t* cnt = scratch + ((kScanSmemWords + 3) & ~3u);  // counters
+    uint32_t* cnt = scratch + kScanWarpWords * (kSparseBatchThreads / 32);  // counters
     const uint32_t ns = h->n_sparse;
     const uint64_t total = ns ? h->sparse_off[ns] : 0;
     // counters start at zero; evaluating an item clears the ones it used.  The
     // launch sized the counters for its largest tile: zero what it allocated.
     const uint32_t cnt_words =
-        dynamic_smem_bytes() / 4 - 2048 - ((kScanSmemWords + 3) & ~3u) - 32;
+        dynamic_smem_bytes() / 4 - 2048 - kScanWarpWords * (kSparseBatchThreads / 32) - 32;
     for (uint32_t i = threadIdx.x; i < cnt_words; i += blockDim.x) cnt[i] = 0u;
     for (;;) {
         if (threadIdx.x == 0) item_s = atomicAdd(&h->sparse_next, 1ull);
@@ -209,8 +211,8 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 2)
         }
         // 8-bit counters hold every count when n <= 255 (the counter-width switch by N)
         const unsigned long long card =
-            n <= 255 ? sparse_item<8>(d, pred, tab, scratch, cnt, cnt_words, tile, pa)
-                     : sparse_item<16>(d, pred, tab, scratch, cnt, cnt_words, tile, pa);
+            n <= 255 ? sparse_item<8>(d, pred, tab, scratch, &s_next, cnt, cnt_words, tile, pa)
+                     : sparse_item<16>(d, pred, tab, scratch, &s_next, cnt, cnt_words, tile, pa);
         block_card_add(card, reinterpret_cast<unsigned long long*>(h->out_cards + qi), part);
         __syncthreads();
     }
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 2)
 // Shared memory of the sparse batch kernel for tiles of up to max_tile rows.
 size_t sparse_batch_smem(uint32_t max_tile) {
     // truth table, scratch, 16-bit counters and one spare word per lane
-    return (2048 + (((size_t)kScanSmemWords + 3) & ~(size_t)3) + (size_t)max_tile / 2 + 32) * 4;
+    return (2048 + (size_t)kScanWarpWords * (kSparseBatchThreads / 32) + (size_t)max_tile / 2 + 32) * 4;
 }
 
 }  // namespace

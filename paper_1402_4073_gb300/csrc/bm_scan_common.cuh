@@ -4,17 +4,20 @@
 // Position lists sit in the pool 16-byte aligned and padded to a multiple of
 // four entries with values outside every tile that could read them, so any
 // aligned 16-byte vector of a list may be read and its four entries filtered
-// by the tile's row range alone.  The tile's slice of every list is found
-// from the pool's per-list tile index and widened to whole vectors.  Lists
-// are taken in chunks of kScanChunk: the CTA loads all slice bounds of a
-// chunk at once, prefix-sums the vector counts (and the number of non-empty
-// slices) in one scan, and so lays the slices end to end as one stream of
-// vectors.  The stream is cut into pieces of 32 vectors; per piece a table
-// holds the slice of its first vector and a bit mask of the slices that
-// start inside it, so lane l of a warp finds the slice of vector 32q + l with
-// one population count.  Warps take pieces in turn, U at a time, each lane
-// loading one 16-byte vector per piece: all lanes are busy however short the
-// slices are, and no lane searches.
+// by the tile's row range alone.  The tile's slice of a list is found from
+// the pool's per-list tile index and widened to whole vectors.
+//
+// Warps take groups of 32 lists: each warp's first group is fixed, the rest
+// come from a shared counter, so warps that drew short slices take more
+// groups.  In a group, lane k loads the slice bounds of list k (the next
+// group's bounds are in flight while this one is counted), a warp scan lays
+// the 32 slices end to end as one stream of vectors, and the stream is read
+// in pieces of 32 vectors, one per lane: the slice holding lane l's vector
+// is found with one ballot (slices begun before the piece), one OR-reduction
+// (slices beginning inside it) and a population count, so all lanes load
+// whatever the slice lengths.  The loads of the next U pieces are issued
+// before the increments of the current U.  No block-wide barrier is taken
+// while counting.
 #pragma once
 
 #include "bm_device.cuh"
@@ -22,57 +25,9 @@
 namespace bm {
 namespace dev {
 
-constexpr uint32_t kScanChunk = 1024;   // lists per chunk
-constexpr uint32_t kPieceTable = 1024;  // pieces per pass of the piece table
-// shared words the helper needs besides the counters: packed scan values
-// (64-bit, kScanChunk + 1), warp totals (64-bit, 32), slice starts by list,
-// slice starts and stream offsets by rank (+1), piece masks, piece bases
-// (16-bit)
-constexpr uint32_t kScanSmemWords = 2 * (kScanChunk + 1) + 2 * 32 + kScanChunk + kScanChunk +
-                                    (kScanChunk + 1) + kPieceTable + kPieceTable / 2;
-
-// In-place exclusive prefix sum of v[0..m) (64-bit), v[m] = total
-// (m <= kScanChunk, blockDim.x a multiple of 32, at most 1024).
-__device__ __forceinline__ void block_exclusive_scan64(uint64_t* v, uint32_t m,
-                                                       uint64_t* warp_tot) {
-    const uint32_t T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const uint32_t nw = T >> 5;
-    const uint32_t E = (kScanChunk + T - 1) / T;
-    uint64_t s = 0;
-    for (uint32_t e = 0; e < E; ++e) {
-        const uint32_t i = t * E + e;
-        if (i < m) s += v[i];
-    }
-    uint64_t x = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= (uint32_t)o) x += y;
-    }
-    if (lane == 31) warp_tot[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint64_t w = lane < nw ? warp_tot[lane] : 0ull;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
-            if (lane >= (uint32_t)o) w += y;
-        }
-        if (lane < nw) warp_tot[lane] = w;  // inclusive totals per warp
-    }
-    __syncthreads();
-    uint64_t prefix = (warp ? warp_tot[warp - 1] : 0ull) + x - s;
-    for (uint32_t e = 0; e < E; ++e) {
-        const uint32_t i = t * E + e;
-        if (i < m) {
-            const uint64_t a = v[i];
-            v[i] = prefix;
-            prefix += a;
-        }
-    }
-    if (t == 0) v[m] = warp_tot[nw - 1];
-    __syncthreads();
-}
+constexpr uint32_t kScanWarpWords = 64;  // shared words per warp: a group's slices
+// shared words the helper needs besides the counters (up to 32 warps)
+constexpr uint32_t kScanSmemWords = kScanWarpWords * 32;
 
 // Add the four entries of a vector that lie in rows [lo, lo + nrows).  An
 // entry outside the range (alignment or padding of a slice) goes to the
@@ -93,82 +48,96 @@ __device__ __forceinline__ void count_vec(uint32_t* cnt, const uint4& x, uint32_
 
 // Add every position of rows [lo, lo + nrows) of lists ids[0..n) into
 // BITS-bit counters cnt (packed 32 / BITS per word; cnt_rows / (32 / BITS)
-// words for rows, then 32 spare words).  t0, t1: tile-index
-// entries bounding the tile.  vpos: the pool's list arena as 16-byte
-// vectors.  scratch: kScanSmemWords shared words, 16-byte aligned.
+// words for rows, then 32 spare words).  t0, t1: tile-index entries bounding
+// the tile.  vpos: the pool's list arena as 16-byte vectors.  scratch:
+// kScanWarpWords shared words per warp.  s_next: a shared word.  Every
+// thread of the block calls this; it begins with a block barrier.
 template <int BITS, int U>
-__device__ __forceinline__ void count_tile(uint32_t* cnt, uint32_t* scratch, const uint32_t* ids,
-                                           uint32_t n, const uint4* vpos,
+__device__ __forceinline__ void count_tile(uint32_t* cnt, uint32_t* scratch, uint32_t* s_next,
+                                           const uint32_t* ids, uint32_t n, const uint4* vpos,
                                            const uint64_t* list_begin,
                                            const uint32_t* tile_index, uint32_t tiles_per_list,
                                            uint64_t t0, uint64_t t1, uint32_t lo,
                                            uint32_t nrows, uint32_t cnt_rows) {
-    uint64_t* s_scan = reinterpret_cast<uint64_t*>(scratch);  // kScanChunk + 1: (vectors, non-empty)
-    uint64_t* s_wt = s_scan + kScanChunk + 1;                  // 32
-    uint32_t* s_vsj = reinterpret_cast<uint32_t*>(s_wt + 32);  // kScanChunk: first vector, by list
-    uint32_t* s_vs = s_vsj + kScanChunk;                       // kScanChunk: first vector, by rank
-    uint32_t* s_off = s_vs + kScanChunk;                       // kScanChunk + 1: stream offset, by rank
-    uint32_t* s_mask = s_off + kScanChunk + 1;                 // kPieceTable: slice starts in a piece
-    uint16_t* s_base = reinterpret_cast<uint16_t*>(s_mask + kPieceTable);  // kPieceTable
-    const uint32_t T = blockDim.x;
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = T >> 5;
-    const uint32_t below = ((2u << lane) - 1u) & ~1u;  // lanes 1..lane of a piece
+    constexpr uint32_t kFull = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t le = (2u << lane) - 1u, lt = (1u << lane) - 1u;
     const uint32_t spare = cnt_rows + lane * (32 / BITS);  // this lane's spare counter word
-    for (uint32_t c0 = 0; c0 < n; c0 += kScanChunk) {
-        const uint32_t m = min(kScanChunk, n - c0);
-        for (uint32_t j = threadIdx.x; j < m; j += T) {
-            const uint32_t id = __ldg(ids + c0 + j);
+    const uint32_t ngroups = (n + 31) / 32;
+    uint32_t* ws = scratch + warp * kScanWarpWords;  // [0,32): first vector, [32,64): offset
+    if (threadIdx.x == 0) *s_next = nw;
+    __syncthreads();
+    // slice of list 32 g + lane: first vector vs, vectors nv (0: empty)
+    auto bounds = [&](uint32_t g, uint32_t& vs, uint32_t& nv) {
+        vs = 0u;
+        nv = 0u;
+        const uint32_t j = g * 32 + lane;
+        if (g < ngroups && j < n) {
+            const uint32_t id = __ldg(ids + j);
             const uint32_t* idx = tile_index + (uint64_t)id * (tiles_per_list + 1);
             const uint32_t b = __ldg(idx + t0), en = __ldg(idx + t1);
             const uint64_t base = __ldg(list_begin + id);
-            const uint32_t vs = (uint32_t)((base + b) >> 2);
-            const uint32_t nv = b < en ? (uint32_t)((base + en + 3) >> 2) - vs : 0u;
-            s_vsj[j] = vs;
-            s_scan[j] = ((uint64_t)nv << 32) | (nv ? 1u : 0u);
+            vs = (uint32_t)((base + b) >> 2);
+            nv = b < en ? (uint32_t)((base + en + 3) >> 2) - vs : 0u;
         }
-        __syncthreads();
-        block_exclusive_scan64(s_scan, m, s_wt);
-        const uint32_t total = (uint32_t)(s_scan[m] >> 32);  // vectors in the stream
-        const uint32_t slices = (uint32_t)s_scan[m];         // non-empty slices
-        for (uint32_t j = threadIdx.x; j < m; j += T) {
-            const uint64_t a = s_scan[j];
-            if (s_scan[j + 1] != a) {  // non-empty: rank = slices before it
-                s_vs[(uint32_t)a] = s_vsj[j];
-                s_off[(uint32_t)a] = (uint32_t)(a >> 32);
-            }
+    };
+    uint32_t g = warp, vs, nv;
+    bounds(g, vs, nv);
+    while (g < ngroups) {
+        uint32_t gn = 0;
+        if (lane == 0) gn = atomicAdd(s_next, 1u);
+        gn = __shfl_sync(kFull, gn, 0);
+        uint32_t vs_n, nv_n;
+        bounds(gn, vs_n, nv_n);  // in flight while this group is counted
+        uint32_t inc = nv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= (uint32_t)o) inc += y;
         }
-        if (threadIdx.x == 0) s_off[slices] = total;
+        const uint32_t start = inc - nv;                      // stream offset of this slice
+        const uint32_t total = __shfl_sync(kFull, inc, 31);   // vectors in the stream
+        const uint32_t ne = __ballot_sync(kFull, nv != 0u);   // non-empty slices
+        if (nv) {  // non-empty slices by rank
+            const uint32_t rk = __popc(ne & lt);
+            ws[rk] = vs;
+            ws[32 + rk] = start;
+        }
+        __syncwarp();
         const uint32_t pieces = (total + 31) / 32;
-        for (uint32_t p0 = 0; p0 < pieces; p0 += kPieceTable) {
-            const uint32_t p1 = min(pieces, p0 + kPieceTable);
-            __syncthreads();  // offsets visible; the previous pass is done with the tables
-            for (uint32_t q = threadIdx.x; q < p1 - p0; q += T) s_mask[q] = 0u;
-            __syncthreads();
-            for (uint32_t r = threadIdx.x; r < slices; r += T) {
-                const uint32_t a = s_off[r], z = s_off[r + 1];  // a < z
-                if (a / 32 >= p0 && a / 32 < p1) atomicOr(&s_mask[a / 32 - p0], 1u << (a % 32));
-                // pieces whose first vector lies in this slice
-                const uint32_t qa = max((a + 31) / 32, p0), qz = min((z - 1) / 32 + 1, p1);
-                for (uint32_t q = qa; q < qz; ++q) s_base[q - p0] = (uint16_t)r;
-            }
-            __syncthreads();
-            for (uint32_t q0 = p0 + warp * U; q0 < p1; q0 += nw * U) {
-                uint4 x[U];
+        auto fetch = [&](uint32_t q0, uint4 (&x)[U]) {
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const uint32_t q = q0 + u;
+            for (int u = 0; u < U; ++u) {
+                const uint32_t q = q0 + u;
+                x[u] = make_uint4(lo - 1u, lo - 1u, lo - 1u, lo - 1u);  // outside the tile
+                if (q < pieces) {  // uniform across the warp
+                    // rank of the slice holding vector 32 q + lane
+                    const uint32_t before = __popc(__ballot_sync(kFull, nv != 0u && start < q * 32));
+                    const uint32_t inside = __reduce_or_sync(
+                        kFull, (nv != 0u && (start >> 5) == q) ? (1u << (start & 31)) : 0u);
+                    const uint32_t r = before + __popc(inside & le) - 1u;
                     const uint32_t v = q * 32 + lane;
-                    x[u] = make_uint4(lo - 1u, lo - 1u, lo - 1u, lo - 1u);  // outside the tile
-                    if (q < p1 && v < total) {
-                        const uint32_t r = s_base[q - p0] + __popc(s_mask[q - p0] & below);
-                        x[u] = ld_stream(vpos + s_vs[r] + (v - s_off[r]));
-                    }
+                    if (v < total) x[u] = ld_stream(vpos + ws[r] + (v - ws[32 + r]));
                 }
-#pragma unroll
-                for (int u = 0; u < U; ++u) count_vec<BITS>(cnt, x[u], lo, nrows, spare);
             }
+        };
+        auto add = [&](const uint4 (&x)[U]) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) count_vec<BITS>(cnt, x[u], lo, nrows, spare);
+        };
+        uint4 xa[U], xb[U];
+        fetch(0, xa);
+        for (uint32_t q0 = 0; q0 < pieces; q0 += 2 * U) {
+            if (q0 + U < pieces) fetch(q0 + U, xb);
+            add(xa);
+            if (q0 + U >= pieces) break;
+            if (q0 + 2 * U < pieces) fetch(q0 + 2 * U, xa);
+            add(xb);
         }
-        __syncthreads();
+        __syncwarp();  // the group's slices are read before the next group writes them
+        g = gn;
+        vs = vs_n;
+        nv = nv_n;
     }
 }
 

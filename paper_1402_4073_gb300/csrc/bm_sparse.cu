@@ -43,16 +43,17 @@ __device__ void build_truth(const Pred& pr, uint32_t n, uint32_t* tab, uint32_t 
     }
 }
 
-// Three CTAs of 8-bit counters fit on an SM at 32768-row tiles; eight pieces
-// in flight need more than the 40 registers that three 512-thread CTAs leave.
-template <int BITS, int U>  // counter width: 8 or 16; pieces in flight per warp
-__global__ void __launch_bounds__(512, (BITS == 8 && U <= 4) ? 3 : 2) scancount_kernel(SparseArgs a) {
+// Two 512-thread CTAs per SM: the pipelined loads need the 64 registers
+// that leaves.
+template <int BITS, int U>  // counter width: 8 or 16; pieces per load batch
+__global__ void __launch_bounds__(512, 2) scancount_kernel(SparseArgs a) {
     extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ uint32_t s_next;  // next group of lists to count
     constexpr uint32_t kPer = 32 / BITS;  // counters per 32-bit word
     const uint32_t tab_words = (a.n + 1 + 31) / 32;
     uint32_t* tab = sm;
     uint32_t* scratch = sm + ((tab_words + 3) & ~3u);
-    uint32_t* cnt = scratch + ((kScanSmemWords + 3) & ~3u);
+    uint32_t* cnt = scratch + kScanWarpWords * (blockDim.x / 32);
     const uint32_t cnt_words = a.tile_rows / kPer;
     build_truth(a.pred, a.n, tab, tab_words);
 
@@ -68,7 +69,8 @@ __global__ void __launch_bounds__(512, (BITS == 8 && U <= 4) ? 3 : 2) scancount_
         const uint64_t hi = min(lo + a.tile_rows, a.r_bits);
         const uint64_t t0 = tile * sub;
         const uint64_t t1 = (t0 + sub < a.tiles_per_list) ? t0 + sub : (uint64_t)a.tiles_per_list;
-        count_tile<BITS, U>(cnt, scratch, a.ids, a.n, reinterpret_cast<const uint4*>(a.positions),
+        count_tile<BITS, U>(cnt, scratch, &s_next, a.ids, a.n,
+                            reinterpret_cast<const uint4*>(a.positions),
                             a.list_begin, a.tile_index, a.tiles_per_list, t0, t1, (uint32_t)lo,
                             (uint32_t)(hi - lo), a.tile_rows);
         __syncthreads();
@@ -100,11 +102,11 @@ int launch_sparse(const SparseArgs& a, const SparseConfig& cfg, int sm_count, cu
     if (a.tile_rows == 0 || a.tile_rows % kListTileRows || a.tile_rows > 65536) return BM_EINVAL;
     const int bits = a.n <= 255 ? 8 : 16;
     const size_t tab_words = ((size_t)(a.n + 1 + 31) / 32 + 3) & ~(size_t)3;
-    const size_t scratch_words = ((size_t)dev::kScanSmemWords + 3) & ~(size_t)3;
+    const int threads = std::max(64, std::min(512, cfg.threads)) & ~31;
+    const size_t scratch_words = (size_t)dev::kScanWarpWords * (size_t)(threads / 32);
     // counters, then one spare word per lane
     const size_t smem = (tab_words + scratch_words + (size_t)a.tile_rows * bits / 32 + 32) * 4;
     const uint64_t ntiles = (a.r_bits + a.tile_rows - 1) / a.tile_rows;
-    const int threads = std::max(64, std::min(512, cfg.threads));
     const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(ntiles, cap));
     auto go = [&](auto fn) -> int {
@@ -115,8 +117,8 @@ int launch_sparse(const SparseArgs& a, const SparseConfig& cfg, int sm_count, cu
         BM_CUDA_TRY(cudaGetLastError());
         return BM_OK;
     };
-    if (cfg.unroll >= 8)
-        return bits == 8 ? go(scancount_kernel<8, 8>) : go(scancount_kernel<16, 8>);
+    if (cfg.unroll <= 2)
+        return bits == 8 ? go(scancount_kernel<8, 2>) : go(scancount_kernel<16, 2>);
     return bits == 8 ? go(scancount_kernel<8, 4>) : go(scancount_kernel<16, 4>);
 }
 

@@ -20,13 +20,17 @@ struct Tuned {
     bool has_sparse = false;
 };
 
+// Bumped whenever kernel shapes or their parameters change meaning, so that
+// entries tuned for other kernels are not reused.
+constexpr int kTuneVersion = 2;
+
 std::string cache_key(const bm_pool* p, bool lists) {
     cudaDeviceProp prop{};
     cudaGetDeviceProperties(&prop, p->device);
     std::ostringstream k;
     std::string name = prop.name;
     std::replace(name.begin(), name.end(), ' ', '_');
-    k << name << "/sm" << prop.multiProcessorCount << "/r" << p->r_bits << "/lists" << (lists ? 1 : 0);
+    k << "v" << kTuneVersion << "/" << name << "/sm" << prop.multiProcessorCount << "/r" << p->r_bits << "/lists" << (lists ? 1 : 0);
     return k.str();
 }
 
@@ -171,7 +175,7 @@ extern "C" int bm_pool_autotune(bm_pool* p, const char* cache_path, char* report
             for (uint32_t tile : {16384u, 32768u, 65536u})
                 for (int th : {256, 512})
                     for (int ct : {1, 2, 4})
-                    for (int un : {4, 8}) {
+                    for (int un : {2, 4}) {
                         bm_sparse_config_t c{tile, th, ct, un};
                         if (bm_pool_set_sparse_config(p, &c)) continue;
                         rc = time_us(s, [&] { return bm_query_run(p, &sq, cards, nullptr, s); }, &tt);
