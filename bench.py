@@ -283,6 +283,60 @@ def bench_selector(bm, datagen, n_train: int = 600, small: bool = False):
     return out
 
 
+def bench_sparse(bm, datagen, reps: int = 20, small: bool = False, config: str = ""):
+    """ScanCount alone (Sec. 4.2): single queries over the position lists of a
+    1500 x 2^24 pool (densities log-uniform [1e-5,1e-2]); N = 1500, 537, 128
+    and 16 random lists, theta = min(N, 8).  Per N: CUDA-event time per
+    launch and its fraction of the HBM peak for the algorithmic bytes 4 B +
+    r/8 (B = listed positions read, the output written).  small: 2^22 rows."""
+    import numpy as np
+    import torch
+    r_bits, nbm = ((1 << 22) if small else (1 << 24)), 1500
+    words, flat, offs, _ = datagen.sparse_pool(nbm, r_bits)
+    pool = bm.Pool(r_bits, nbm)
+    pool.put_dense(words)
+    pool.put_positions(flat, offs)
+    del words, flat
+    if config:
+        pool.set_sparse_config(*[int(x) for x in config.split(",")])
+        tune = "fixed by --sparse-config"
+    else:
+        tune = pool.autotune()
+    lens = offs[1:].astype(np.int64) - offs[:-1].astype(np.int64)
+    peak, peak_src = peaks()
+    out = pool.empty_words()
+    card = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+    for n in (1500, 537, 128, 16):
+        ids = datagen.floyd(datagen.STREAM_SPARSE + (9 << 32) + n, nbm, n)
+        q = datagen.Query(ids, datagen.KIND_THRESHOLD, theta=min(n, 8))
+        pq = bm.PreparedQuery(pool, q, out, bm.PATH_SPARSE)
+        for _ in range(3):
+            pq.run(card)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        torch.cuda.synchronize()
+        for i in range(reps):
+            ev[2 * i].record(stream)
+            pq.run(card)
+            ev[2 * i + 1].record(stream)
+        torch.cuda.synchronize()
+        us = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(reps)) * 1e3
+        b = int(lens[ids].sum())
+        alg = 4 * b + r_bits // 8
+        rows.append({"N": n, "positions": b, "us_per_query": round(us, 1),
+                     "achieved_GBps": round(alg / us / 1e3, 1),
+                     "frac": round(alg / us / 1e3 / peak, 4)})
+    pool.status()
+    pool.close()
+    return {"workload": f"sparse single queries: {nbm} x 2^{r_bits.bit_length() - 1} pool "
+                        "(densities log-uniform [1e-5,1e-2], position lists), theta=min(N,8)",
+            "kernel": "ScanCount (scancount_kernel)", "bytes": "4 * positions + r/8 per query",
+            "peak": peak, "peak_source": f"hbm_gbs of {peak_src}",
+            "timing": f"median of {reps} launches, CUDA events around each bm_query_run",
+            "queries": rows, "autotune": tune}
+
+
 def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds: float = 0.8,
                   small: bool = False):
     """Serving loop on the 10,000 x 2^22 pool: Poisson arrivals at each
@@ -383,8 +437,10 @@ def main():
                     help="rows = 2^r_log2 (smaller cases are for profiling only)")
     ap.add_argument("--dense-config", default="",
                     help="variant,threads,stages,ctas_per_sm[,adder]: skip the variant search")
-    ap.add_argument("--parts", default="dense,batch,selector,serving",
-                    help="comma list of dense, batch, selector, serving")
+    ap.add_argument("--parts", default="dense,sparse,batch,selector,serving",
+                    help="comma list of dense, sparse, batch, selector, serving")
+    ap.add_argument("--sparse-config", default="",
+                    help="tile_rows,threads,ctas_per_sm,unroll for the sparse part: skip tuning")
     ap.add_argument("--small", action="store_true",
                     help="scaled-down batch/selector/serving workloads (profiling only)")
     args = ap.parse_args()
@@ -507,6 +563,8 @@ def main():
     pool.close()
     extra = {}
     parts = args.parts.split(",")
+    if "sparse" in parts:
+        extra["sparse"] = bench_sparse(bm, datagen, small=args.small, config=args.sparse_config)
     if "batch" in parts:
         extra["batched"] = bench_batched(bm, datagen, small=args.small)
     if "selector" in parts:
