@@ -95,8 +95,14 @@ int bm_pool_put_dense(bm_pool* pool, uint32_t first_id, uint32_t count, const ui
  * increasing and every position < r (checked on the host for host input,
  * by a device check kernel for device input; BM_ERANGE otherwise).  A
  * per-list tile index (first list entry at each multiple of 8192 rows) is
- * built on the device.  Synchronous.  A list loaded for an id replaces any
- * earlier list of that id.
+ * built on the device.  In the pool each list starts 16-byte aligned and is
+ * padded to a multiple of four entries (at most three extra entries per
+ * list), which the sparse kernels read as whole 16-byte vectors.  Host input
+ * passes through a temporary device copy of `count` lists' entries.
+ * Synchronous.  A list loaded for an id replaces any earlier list of that id
+ * (the earlier list's arena space is not reused).
+ * Errors: BM_ENOMEM when the arena would pass 2^32 entries or the memory
+ * budget.
  */
 int bm_pool_put_positions(bm_pool* pool, uint32_t first_id, uint32_t count,
                           const uint32_t* positions, const uint64_t* offsets,

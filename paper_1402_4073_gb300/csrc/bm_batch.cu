@@ -22,10 +22,11 @@
 namespace bm {
 
 constexpr int kBatchThreads = 256;        // dense: one 16-byte column per thread
-constexpr int kSparseBatchThreads = 512;
-// Batched sparse items use tiles of at most 32768 rows, so that two sparse
-// CTAs (16-bit counters) fit on an SM whatever tile a query would take alone.
-constexpr uint32_t kSparseMaxTile = 32768;
+constexpr int kSparseBatchThreads = 384;
+// Batched sparse items use at most 16384 counter words (32768 rows of 16-bit
+// counters, 65536 rows of 8-bit ones), so that two sparse CTAs fit on an SM
+// whatever tile a query would take alone.
+constexpr uint32_t kSparseMaxWords = 16384;
 // Pieces per load batch of a warp in batched ScanCount items (two batches
 // in flight; they fit in the 64 registers two 512-thread CTAs per SM leave).
 constexpr int kSparseBatchUnroll = 2;
@@ -168,21 +169,44 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 2)
     const uint32_t cnt_words =
         dynamic_smem_bytes() / 4 - 2048 - kScanWarpWords * (kSparseBatchThreads / 32) - 32;
     for (uint32_t i = threadIdx.x; i < cnt_words; i += blockDim.x) cnt[i] = 0u;
+    __shared__ uint32_t query_s;  // the query of this CTA's current (then previous) item
+    // thread 0 fetches each next item while the current one is counted
+    unsigned long long pending = 0;
+    if (threadIdx.x == 0) {
+        query_s = 0;
+        pending = atomicAdd(&h->sparse_next, 1ull);
+    }
     for (;;) {
-        if (threadIdx.x == 0) item_s = atomicAdd(&h->sparse_next, 1ull);
+        if (threadIdx.x == 0) {
+            const unsigned long long it = pending;
+            item_s = it;
+            if (it < total) {
+                pending = atomicAdd(&h->sparse_next, 1ull);
+                // the query of this item is the last prefix entry <= it.  A CTA's
+                // items increase, so gallop forward from its previous query, then
+                // bisect: a few dependent loads instead of log2(n_sparse)
+                uint32_t lo = query_s, hi = lo + 1, step = 1;
+                while (hi < ns && h->sparse_off[hi] <= it) {
+                    lo = hi;
+                    step *= 2;
+                    hi = lo + step;
+                }
+                if (hi > ns) hi = ns;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) / 2;
+                    if (h->sparse_off[mid] <= it)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                query_s = lo;
+            }
+        }
         __syncthreads();
         const uint64_t item = item_s;
+        const uint32_t lo = query_s;
         __syncthreads();
         if (item >= total) break;
-        // query of this item: last prefix entry <= item
-        uint32_t lo = 0, hi = ns;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) / 2;
-            if (h->sparse_off[mid] <= item)
-                lo = mid;
-            else
-                hi = mid;
-        }
         const uint32_t qi = h->sparse_list[lo];
         const QueryDesc* d = h->desc + qi;
         const uint32_t n = d->n;
@@ -218,10 +242,11 @@ __global__ void __launch_bounds__(kSparseBatchThreads, 2)
     }
 }
 
-// Shared memory of the sparse batch kernel for tiles of up to max_tile rows.
-size_t sparse_batch_smem(uint32_t max_tile) {
+// Shared memory of the sparse batch kernel with `words` 32-bit counter words
+// (rows x counter bits / 32 of its largest item).
+size_t sparse_batch_smem(uint32_t words) {
     // truth table, scratch, 16-bit counters and one spare word per lane
-    return (2048 + (size_t)kScanWarpWords * (kSparseBatchThreads / 32) + (size_t)max_tile / 2 + 32) * 4;
+    return (2048 + (size_t)kScanWarpWords * (kSparseBatchThreads / 32) + (size_t)words + 32) * 4;
 }
 
 }  // namespace
@@ -304,11 +329,12 @@ static int slot_reserve(bm_pool* p, BatchSlot& sl, size_t bytes) {
     return BM_OK;
 }
 
-static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, uint32_t max_tile,
+static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, uint32_t max_words,
                      const BatchPoolArgs& pa, cudaGraphExec_t* out) {
     const int adder = b->cfg.adder, L = b->cfg.words_per_thread == 1 ? 2 : 4;
-    const int tile_code = max_tile <= 16384 ? 0 : max_tile <= 32768 ? 1 : 2;
-    const uint32_t tile_cap = 16384u << tile_code;
+    // counter words of the largest sparse item: 8192 or kSparseMaxWords
+    const int tile_code = max_words <= kSparseMaxWords / 2 ? 0 : 1;
+    const uint32_t words_cap = (kSparseMaxWords / 2) << tile_code;
     const int key = ((K * 64 + adder * 8 + L) << 2) | tile_code;
     auto it = sl.graphs.find(key);
     if (it != sl.graphs.end()) {
@@ -322,7 +348,7 @@ static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, uint32_t m
         BM_CUDA_TRY(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
     }
     BatchHeader* h = static_cast<BatchHeader*>(sl.d);
-    const size_t sp_smem = sparse_batch_smem(tile_cap);
+    const size_t sp_smem = sparse_batch_smem(words_cap);
     int optin = 0;
     BM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
     const unsigned dense_grid = (unsigned)(p->sm_count * std::max(1, b->cfg.ctas_per_sm));
@@ -357,7 +383,7 @@ static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, uint32_t m
     };
     BM_CUDA_TRY(cudaFuncSetAttribute(sparse_batch_kernel,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sparse_batch_smem(kSparseMaxTile)));
+                                     (int)sparse_batch_smem(kSparseMaxWords)));
 #define BM_BATCH_DISPATCH(LL)                                                      \
     if (adder == 2 && LL == 4) {                                                   \
         if (K <= 5) return dense_fn(dense_batch_kernel<5, 16, 4>);                 \
@@ -489,13 +515,16 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
     std::vector<Pred> preds(nq);
     std::vector<uint32_t> dense_list, sparse_list;
     std::vector<uint64_t> sparse_off(1, 0);
-    uint32_t max_tile = 0;
+    uint32_t max_words = 0;
     for (uint32_t i = 0; i < nq; ++i) {
         preds[i] = compile_pred(truth[i].data(), q[i].n);
         if (preds[i].mode == 2) total_tab += preds[i].table_words32;
         if (cand[i].path == BM_PATH_SPARSE) {
-            if (cand[i].tile_rows > kSparseMaxTile) cand[i].tile_rows = kSparseMaxTile;
-            max_tile = std::max(max_tile, cand[i].tile_rows);
+            // 8-bit items (n <= 255) fit twice the rows in the same counter words
+            const uint32_t bits = q[i].n <= 255 ? 8u : 16u;
+            const uint32_t cap = kSparseMaxWords * (32 / bits);
+            if (cand[i].tile_rows > cap) cand[i].tile_rows = cap;
+            max_words = std::max(max_words, cand[i].tile_rows * bits / 32);
             sparse_list.push_back(i);
             sparse_off.push_back(sparse_off.back() +
                                  (p->r_bits + cand[i].tile_rows - 1) / cand[i].tile_rows);
@@ -574,7 +603,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
     const int K = planes_for(max_dense_n);
     const int kk = K <= 5 ? 5 : K <= 9 ? 9 : K <= 11 ? 11 : K <= 13 ? 13 : 17;
     cudaGraphExec_t ex = nullptr;
-    rc = graph_for(p, b, sl, kk, max_tile, pa, &ex);
+    rc = graph_for(p, b, sl, kk, max_words, pa, &ex);
     if (rc) return rc;
     BM_CUDA_TRY(cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, s));
     BM_CUDA_TRY(cudaGraphLaunch(ex, s));

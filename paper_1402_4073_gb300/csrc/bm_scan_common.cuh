@@ -9,7 +9,8 @@
 //
 // Warps take groups of 32 lists: each warp's first group is fixed, the rest
 // come from a shared counter, so warps that drew short slices take more
-// groups.  In a group, lane k loads the slice bounds of list k (the next
+// groups; with fewer groups than warps, teams of warps share a group's
+// pieces.  In a group, lane k loads the slice bounds of list k (the next
 // group's bounds are in flight while this one is counted), a warp scan lays
 // the 32 slices end to end as one stream of vectors, and the stream is read
 // in pieces of 32 vectors, one per lane: the slice holding lane l's vector
@@ -81,14 +82,20 @@ __device__ __forceinline__ void count_tile(uint32_t* cnt, uint32_t* scratch, uin
             nv = b < en ? (uint32_t)((base + en + 3) >> 2) - vs : 0u;
         }
     };
-    uint32_t g = warp, vs, nv;
-    bounds(g, vs, nv);
-    while (g < ngroups) {
-        uint32_t gn = 0;
-        if (lane == 0) gn = atomicAdd(s_next, 1u);
-        gn = __shfl_sync(kFull, gn, 0);
+    // With fewer groups than warps, a team of `team` warps shares each group,
+    // member m taking pieces m, m + team, ...: work unit u = (group u / team,
+    // member u % team).
+    uint32_t team = 1;
+    while (ngroups && team * 2 * ngroups <= nw) team *= 2;
+    const uint32_t units = ngroups * team;
+    uint32_t u = warp, vs, nv;
+    bounds(u / team, vs, nv);
+    while (u < units) {
+        uint32_t un = 0;
+        if (lane == 0) un = atomicAdd(s_next, 1u);
+        un = __shfl_sync(kFull, un, 0);
         uint32_t vs_n, nv_n;
-        bounds(gn, vs_n, nv_n);  // in flight while this group is counted
+        bounds(un < units ? un / team : ngroups, vs_n, nv_n);  // in flight while this unit is counted
         uint32_t inc = nv;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -105,88 +112,97 @@ __device__ __forceinline__ void count_tile(uint32_t* cnt, uint32_t* scratch, uin
         }
         __syncwarp();
         const uint32_t pieces = (total + 31) / 32;
-        auto fetch = [&](uint32_t q0, uint4 (&x)[U]) {
+        const uint32_t member = u % team;
+        // this warp's pieces: member + k * team, k = 0, 1, ...
+        const uint32_t mine = pieces > member ? (pieces - member + team - 1) / team : 0u;
+        auto fetch = [&](uint32_t k0, uint4 (&x)[U]) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t q = q0 + u;
-                x[u] = make_uint4(lo - 1u, lo - 1u, lo - 1u, lo - 1u);  // outside the tile
-                if (q < pieces) {  // uniform across the warp
+            for (int i = 0; i < U; ++i) {
+                const uint32_t q = member + (k0 + i) * team;
+                x[i] = make_uint4(lo - 1u, lo - 1u, lo - 1u, lo - 1u);  // outside the tile
+                if (k0 + i < mine) {  // uniform across the warp
                     // rank of the slice holding vector 32 q + lane
                     const uint32_t before = __popc(__ballot_sync(kFull, nv != 0u && start < q * 32));
                     const uint32_t inside = __reduce_or_sync(
                         kFull, (nv != 0u && (start >> 5) == q) ? (1u << (start & 31)) : 0u);
                     const uint32_t r = before + __popc(inside & le) - 1u;
                     const uint32_t v = q * 32 + lane;
-                    if (v < total) x[u] = ld_stream(vpos + ws[r] + (v - ws[32 + r]));
+                    if (v < total) x[i] = ld_stream(vpos + ws[r] + (v - ws[32 + r]));
                 }
             }
         };
         auto add = [&](const uint4 (&x)[U]) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) count_vec<BITS>(cnt, x[u], lo, nrows, spare);
+            for (int i = 0; i < U; ++i) count_vec<BITS>(cnt, x[i], lo, nrows, spare);
         };
         uint4 xa[U], xb[U];
         fetch(0, xa);
-        for (uint32_t q0 = 0; q0 < pieces; q0 += 2 * U) {
-            if (q0 + U < pieces) fetch(q0 + U, xb);
+        for (uint32_t k0 = 0; k0 < mine; k0 += 2 * U) {
+            if (k0 + U < mine) fetch(k0 + U, xb);
             add(xa);
-            if (q0 + U >= pieces) break;
-            if (q0 + 2 * U < pieces) fetch(q0 + 2 * U, xa);
+            if (k0 + U >= mine) break;
+            if (k0 + 2 * U < mine) fetch(k0 + 2 * U, xa);
             add(xb);
         }
-        __syncwarp();  // the group's slices are read before the next group writes them
-        g = gn;
+        __syncwarp();  // the group's slices are read before the next unit writes them
+        u = un;
         vs = vs_n;
         nv = nv_n;
     }
 }
 
-// One 32-bit output lane from 32 counters (words cw[0 .. kWords)), which
-// are cleared as they are read, ready for the next tile.  Lane l
-// reads its words starting at word l mod kWords, so at each step the 32
-// lanes of a warp hit (at most two-way) distinct banks instead of all
-// reading the same two banks.  A plain threshold (v0 = 0, one transition
-// theta) compares packed counters with SIMD byte/halfword compares; every
-// other predicate looks f up.
+// One 32-bit output lane from 32 counters (words cw[0 .. kWords), 16-byte
+// aligned), which are cleared as they are read, ready for the next tile.
+// The words are read 16 bytes at a time; a chunk whose counters are all zero
+// (most of them, in a sparse tile) yields f(0) for its rows and needs no
+// compare and no clear.  Lane l starts at chunk l mod kChunks, spreading the
+// warp over the banks.  A plain threshold (v0 = 0, one transition theta)
+// compares packed counters with SIMD byte/halfword compares; every other
+// predicate looks f up in `tab`.
 template <int BITS>
 __device__ __forceinline__ uint32_t counters_to_lane(uint32_t* cw, const Pred& pred,
                                                      const uint32_t* tab) {
-    constexpr uint32_t kPer = 32 / BITS, kWords = 32 / kPer;
+    constexpr uint32_t kPer = 32 / BITS, kWords = 32 / kPer, kChunks = kWords / 4;
+    constexpr uint32_t kChunkRows = 4 * kPer;  // rows per 16-byte chunk
+    uint4* c4 = reinterpret_cast<uint4*>(cw);
     const uint32_t rot = threadIdx.x;
+    const bool plain = pred.mode == 1 && pred.ntrans == 1 && pred.v0 == 0;
+    const uint32_t th = pred.trans[0];  // plain: 1 <= theta <= n
+    const uint32_t tw = BITS == 8 ? th * 0x01010101u : th * 0x00010001u;
+    // rows nobody counted: f(0) (0 for a plain threshold)
+    const uint32_t zero_rows = (!plain && (tab[0] & 1u)) ? (1u << kChunkRows) - 1u : 0u;
     uint32_t o = 0;
-    if (pred.mode == 1 && pred.ntrans == 1 && pred.v0 == 0) {
-        const uint32_t th = pred.trans[0];
-        if (BITS == 8) {
-            const uint32_t t4 = th * 0x01010101u;  // theta <= 255 whenever 8-bit counters are used
 #pragma unroll
-            for (uint32_t k = 0; k < kWords; ++k) {
-                const uint32_t w = (k + rot) & (kWords - 1);
-                const uint32_t ge = __vcmpgeu4(cw[w], t4);  // 0xFF per byte where count >= theta
-                cw[w] = 0u;
-                const uint32_t b = ge & 0x01010101u;
-                o |= ((b | (b >> 7) | (b >> 14) | (b >> 21)) & 0xFu) << (4 * w);
-            }
-        } else {
-            const uint32_t t2 = th * 0x00010001u;
-#pragma unroll
-            for (uint32_t k = 0; k < kWords; ++k) {
-                const uint32_t w = (k + rot) & (kWords - 1);
-                const uint32_t ge = __vcmpgeu2(cw[w], t2);  // 0xFFFF per half where count >= theta
-                cw[w] = 0u;
-                o |= ((ge & 1u) | ((ge >> 15) & 2u)) << (2 * w);
-            }
+    for (uint32_t k = 0; k < kChunks; ++k) {
+        const uint32_t c = (k + rot) & (kChunks - 1);
+        const uint4 v = c4[c];
+        if ((v.x | v.y | v.z | v.w) == 0u) {
+            o |= zero_rows << (c * kChunkRows);
+            continue;
         }
-        return o;
-    }
+        c4[c] = make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (uint32_t k = 0; k < kWords; ++k) {
-        const uint32_t w = (k + rot) & (kWords - 1);
-        const uint32_t word = cw[w];
-        cw[w] = 0u;
+        for (uint32_t j = 0; j < 4; ++j) {
+            const uint32_t word = wv[j];
+            const uint32_t shift = (c * 4 + j) * kPer;  // first row of this word in the lane
+            uint32_t bits = 0;
+            if (plain) {
+                if (BITS == 8) {
+                    const uint32_t b = __vcmpgeu4(word, tw) & 0x01010101u;  // per byte: count >= theta
+                    bits = (b | (b >> 7) | (b >> 14) | (b >> 21)) & 0xFu;
+                } else {
+                    const uint32_t ge = __vcmpgeu2(word, tw);  // 0xFFFF per half where count >= theta
+                    bits = (ge & 1u) | ((ge >> 15) & 2u);
+                }
+            } else {
 #pragma unroll
-        for (uint32_t s = 0; s < kPer; ++s) {
-            const uint32_t c = (word >> (BITS * s)) & ((1u << BITS) - 1u);
-            o |= ((tab[c >> 5] >> (c & 31u)) & 1u) << (w * kPer + s);
+                for (uint32_t s = 0; s < kPer; ++s) {
+                    const uint32_t cnt = (word >> (BITS * s)) & ((1u << BITS) - 1u);
+                    bits |= ((tab[cnt >> 5] >> (cnt & 31u)) & 1u) << s;
+                }
+            }
+            o |= bits << shift;
         }
     }
     return o;

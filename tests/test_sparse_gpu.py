@@ -60,6 +60,30 @@ def test_scancount_tiles_and_ragged_rows(bm, oracle_lib, dg, tile, r_bits):
         _eq(got, oracle_lib.query(words, q, r_bits), "interval")
 
 
+@pytest.mark.parametrize("shape", [(32768, 512, 2, 2), (32768, 256, 2, 4), (16384, 256, 4, 2),
+                                   (65536, 512, 1, 2), (8192, 64, 8, 4), (65536, 96, 1, 4)])
+def test_scancount_kernel_shapes(bm, oracle_lib, dg, shape):
+    """Every shape the autotuner may pick (tile rows, threads, CTAs/SM,
+    pieces per load batch) gives the same exact result, for both counter
+    widths and a table predicate, with groups that leave warps idle
+    (n < 32 per warp) and groups that span several pieces."""
+    r_bits = 3 * 65536 + 4099
+    pool_n = 400
+    dens = dg.log_uniform(dg.uniform(dg.STREAM_TESTS + 11150, pool_n), 1e-4, 5e-2)
+    words = dg.bernoulli(dg.STREAM_TESTS + 11151, r_bits, dens)
+    flat, offs = dg.positions(words, r_bits)
+    with bm.Pool(r_bits, pool_n) as pool:
+        pool.put_dense(words)
+        pool.put_positions(flat, offs)
+        pool.set_sparse_config(*shape)
+        for n in (3, 40, 255, 256, 400, 1000):
+            ids = (np.arange(n) * 7 % pool_n).astype(np.uint32)
+            for q in (dg.Query(ids, 0, theta=max(1, n // 50)),
+                      dg.Query(ids, 1, lo=2, hi=max(2, n // 20))):
+                got, _ = _run(bm, pool, q, bm.PATH_SPARSE)
+                _eq(got, oracle_lib.query(words, q, r_bits), f"shape={shape} n={n} kind={q.kind}")
+
+
 @pytest.mark.parametrize("N", [2, 255, 256, 300, 4096])
 def test_scancount_counter_width(bm, oracle_lib, dg, N):
     """8-bit counters up to N = 255, 16-bit above; planted rows reach count N."""
