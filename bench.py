@@ -337,6 +337,77 @@ def bench_sparse(bm, datagen, reps: int = 20, small: bool = False, config: str =
             "queries": rows, "autotune": tune}
 
 
+def bench_rle(bm, datagen, reps: int = 10, small: bool = False):
+    """Run-length form with clean-run pruning (Sec. 2.1, 4.1) against the dense
+    path on the same pools: N = 256 bitmaps of r = 2^26 rows, densities
+    max(0.5/k, 1e-4), ones in runs of mean 4096, 256 and 8 rows; the four
+    queries of the main benchmark.  Per pool and query: CUDA-event time per
+    call on each path (median of `reps`), logical input GB/s (N r/8 + r/8 per
+    query), and for the run-length path its algorithmic bytes (the inputs'
+    runs and literal words, 8 bytes each, plus one 4-byte tile summary per
+    input and tile, plus r/8 written) and their fraction of the HBM peak.
+    small: r = 2^22."""
+    import numpy as np
+    import torch
+    r_bits, n = ((1 << 22) if small else (1 << 26)), 256
+    ids = np.arange(n, dtype=np.uint32)
+    queries = [datagen.Query(ids, datagen.KIND_THRESHOLD, theta=2),
+               datagen.Query(ids, datagen.KIND_THRESHOLD, theta=128),
+               datagen.Query(ids, datagen.KIND_THRESHOLD, theta=255),
+               datagen.Query(ids, datagen.KIND_INTERVAL, lo=2, hi=10)]
+    peak, peak_src = peaks()
+    stream = torch.cuda.current_stream()
+    pools = []
+    for mean_run in (4096.0, 256.0, 8.0):
+        words = datagen.runs(datagen.STREAM_CONFIG2, r_bits, datagen.config2_density(n), mean_run)
+        pool = bm.Pool(r_bits, n)
+        pool.put_dense(words)
+        del words
+        pool.put_rle()
+        runs = lits = 0
+        for k in range(n):
+            a, b = pool.rle_info(k)
+            runs, lits = runs + a, lits + b
+        tiles = (pool.words + 255) // 256
+        alg = 8 * (runs + lits) + 4 * n * tiles + r_bits // 8
+        out = pool.empty_words()
+        card = torch.zeros(1, dtype=torch.int64, device="cuda")
+        rows = []
+        for q in queries:
+            t = {}
+            for path in (bm.PATH_DENSE, bm.PATH_RLE):
+                pq = bm.PreparedQuery(pool, q, out, path)
+                for _ in range(3):
+                    pq.run(card)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+                torch.cuda.synchronize()
+                for i in range(reps):
+                    ev[2 * i].record(stream)
+                    pq.run(card)
+                    ev[2 * i + 1].record(stream)
+                torch.cuda.synchronize()
+                t[path] = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1])
+                                            for i in range(reps)) * 1e3
+            logical = query_bytes(n, r_bits)
+            rows.append({"query": f"theta={q.theta}" if q.kind == 0 else f"[{q.lo},{q.hi}]",
+                         "dense_us": round(t[bm.PATH_DENSE], 1), "rle_us": round(t[bm.PATH_RLE], 1),
+                         "dense_logical_GBps": round(logical / t[bm.PATH_DENSE] / 1e3, 1),
+                         "rle_logical_GBps": round(logical / t[bm.PATH_RLE] / 1e3, 1),
+                         "rle_achieved_GBps": round(alg / t[bm.PATH_RLE] / 1e3, 1),
+                         "rle_frac": round(alg / t[bm.PATH_RLE] / 1e3 / peak, 4)})
+        pool.status()
+        pools.append({"mean_run_rows": mean_run, "runs": runs, "literal_words": lits,
+                      "rle_bytes_per_query": alg, "dense_bytes_per_query": query_bytes(n, r_bits),
+                      "queries": rows})
+        pool.close()
+    return {"workload": f"clustered dense: N={n} bitmaps x r=2^{r_bits.bit_length() - 1} rows, "
+                        "densities max(0.5/k,1e-4), ones in runs of the given mean length",
+            "kernel": "rle_kernel (run-length form, clean-run pruning)",
+            "peak": peak, "peak_source": f"hbm_gbs of {peak_src}",
+            "timing": f"median of {reps} calls, CUDA events around each bm_query_run",
+            "pools": pools}
+
+
 def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds: float = 0.8,
                   small: bool = False):
     """Serving loop on the 10,000 x 2^22 pool: Poisson arrivals at each
@@ -437,8 +508,8 @@ def main():
                     help="rows = 2^r_log2 (smaller cases are for profiling only)")
     ap.add_argument("--dense-config", default="",
                     help="variant,threads,stages,ctas_per_sm[,adder]: skip the variant search")
-    ap.add_argument("--parts", default="dense,sparse,batch,selector,serving",
-                    help="comma list of dense, sparse, batch, selector, serving")
+    ap.add_argument("--parts", default="dense,sparse,rle,batch,selector,serving",
+                    help="comma list of dense, sparse, rle, batch, selector, serving")
     ap.add_argument("--sparse-config", default="",
                     help="tile_rows,threads,ctas_per_sm,unroll for the sparse part: skip tuning")
     ap.add_argument("--small", action="store_true",
@@ -565,6 +636,8 @@ def main():
     parts = args.parts.split(",")
     if "sparse" in parts:
         extra["sparse"] = bench_sparse(bm, datagen, small=args.small, config=args.sparse_config)
+    if "rle" in parts:
+        extra["rle"] = bench_rle(bm, datagen, small=args.small)
     if "batch" in parts:
         extra["batched"] = bench_batched(bm, datagen, small=args.small)
     if "selector" in parts:

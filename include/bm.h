@@ -108,6 +108,23 @@ int bm_pool_put_positions(bm_pool* pool, uint32_t first_id, uint32_t count,
                           const uint32_t* positions, const uint64_t* offsets,
                           int positions_on_device);
 
+/*
+ * Build the run-length form of ids first_id .. first_id + count - 1 from their
+ * dense copies (which must be loaded; BM_ERANGE otherwise): the word-aligned
+ * run form of a compressed bitmap (Sec. 2.1, EWAH), i.e. maximal runs of
+ * all-zero words, all-one words and literal words, kept as a run array, a
+ * literal-word array and, per 256-word tile, the run holding the tile's first
+ * word.  Queries on BM_PATH_RLE read only the runs and literal words of
+ * their inputs.  Synchronous (the words pass through host memory once).
+ * Rebuilding an id appends a new form; the earlier one's space is not reused.
+ * Errors: BM_ENOMEM over the memory budget.
+ */
+int bm_pool_put_rle(bm_pool* pool, uint32_t first_id, uint32_t count);
+
+/* Runs (without the terminating sentinel) and literal words of id's
+ * run-length form.  BM_ERANGE if the id has none. */
+int bm_pool_rle_info(const bm_pool* pool, uint32_t id, uint64_t* runs, uint64_t* literal_words);
+
 typedef struct bm_pool_info_t {
     uint64_t r_bits;           /* rows per bitmap */
     uint64_t words;            /* ceil(r / 64) */
@@ -118,6 +135,8 @@ typedef struct bm_pool_info_t {
     uint32_t sm_count;         /* streaming multiprocessors of the pool's device */
     uint64_t device_bytes;     /* device bytes held by the pool */
     const uint64_t* dense_base;/* device address of id 0's dense words */
+    uint32_t rle_loaded;       /* ids holding a run-length form */
+    uint32_t reserved;
 } bm_pool_info_t;
 
 /* Fill *out with the pool's shape. */
@@ -231,6 +250,8 @@ int bm_symmetric(bm_pool* pool, const uint32_t* ids, uint32_t n, const uint64_t*
 #define BM_PATH_AUTO 0   /* the pool's selector chooses (learned model, else a density rule) */
 #define BM_PATH_DENSE 1  /* bit-sliced carry-save counter over the dense words */
 #define BM_PATH_SPARSE 2 /* ScanCount over the position lists (every id needs a list) */
+#define BM_PATH_RLE 3    /* run-length form with clean-run pruning (every id needs one);
+                            single queries only, never chosen by BM_PATH_AUTO */
 
 typedef struct bm_query {
     const uint32_t* ids;    /* host array of n pool ids (repeats allowed) */
@@ -248,7 +269,8 @@ typedef struct bm_query {
  * Run one query on the path it names.  out_card: device uint64 or NULL.
  * *chosen_path (may be NULL) receives the path that ran.  Errors as
  * bm_threshold, plus BM_EINVAL for a bad kind/path and BM_ERANGE when the
- * sparse path is asked for an id without a position list.
+ * sparse (run-length) path is asked for an id without a position list
+ * (run-length form).
  */
 int bm_query_run(bm_pool* pool, const bm_query* q, uint64_t* out_card, int32_t* chosen_path,
                  void* stream);
@@ -266,7 +288,8 @@ int bm_query_run(bm_pool* pool, const bm_query* q, uint64_t* out_card, int32_t* 
  * chosen_paths: host, nq entries (may be NULL), receives each query's path.
  * Every result equals that of the same query run alone.  Host arrays are
  * copied before the call returns; up to three batches may be in flight.
- * Errors as bm_query_run, for the first failing query (nothing is launched).
+ * Errors as bm_query_run, for the first failing query (nothing is launched);
+ * BM_EINVAL for a query on BM_PATH_RLE (single queries only).
  */
 int bm_threshold_batch(bm_pool* pool, const bm_query* q, uint32_t nq, uint64_t* out_cards,
                        int32_t* chosen_paths, void* stream);

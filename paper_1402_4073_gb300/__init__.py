@@ -127,6 +127,21 @@ class Pool:
         check(lib.bm_pool_put_positions(self.handle, first_id, len(offs) - 1, fp, offs.ctypes.data, 0),
               "bm_pool_put_positions")
 
+    def put_rle(self, first_id: int = 0, count: int | None = None) -> None:
+        """Build the run-length form (clean/literal word runs) of dense ids
+        first_id .. first_id + count - 1 (all loaded dense ids from first_id by
+        default) for BM_PATH_RLE queries."""
+        if count is None:
+            count = self.info()["capacity"] - first_id
+        check(lib.bm_pool_put_rle(self.handle, first_id, count), "bm_pool_put_rle")
+
+    def rle_info(self, id_: int) -> tuple[int, int]:
+        """(runs, literal words) of id's run-length form."""
+        r, l = ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib.bm_pool_rle_info(self.handle, id_, ctypes.byref(r), ctypes.byref(l)),
+              "bm_pool_rle_info")
+        return int(r.value), int(l.value)
+
     def info(self) -> dict:
         i = _native.bm_pool_info_t()
         check(lib.bm_pool_info(self.handle, ctypes.byref(i)), "bm_pool_info")
@@ -219,7 +234,7 @@ def to_numpy_words(t: torch.Tensor) -> np.ndarray:
 # query descriptors, path choice, batches
 
 KIND_THRESHOLD, KIND_INTERVAL, KIND_TABLE = 0, 1, 2
-PATH_AUTO, PATH_DENSE, PATH_SPARSE = 0, 1, 2
+PATH_AUTO, PATH_DENSE, PATH_SPARSE, PATH_RLE = 0, 1, 2, 3
 SELECTOR_FEATURES, SELECTOR_HIDDEN, SELECTOR_CANDIDATES = 5, 64, 4
 # candidate c of the selector: (path, sparse tile rows)
 CANDIDATES = [(PATH_DENSE, 0), (PATH_SPARSE, 16384), (PATH_SPARSE, 32768), (PATH_SPARSE, 65536)]

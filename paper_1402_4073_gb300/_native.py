@@ -25,7 +25,7 @@ class bm_query(ctypes.Structure):
 class bm_pool_info_t(ctypes.Structure):
     _fields_ = [("r_bits", u64), ("words", u64), ("stride_words", u64), ("capacity", u32),
                 ("dense_loaded", u32), ("lists_loaded", u32), ("sm_count", u32),
-                ("device_bytes", u64), ("dense_base", vp)]
+                ("device_bytes", u64), ("dense_base", vp), ("rle_loaded", u32), ("reserved", u32)]
 
 
 class bm_dense_config_t(ctypes.Structure):
@@ -62,6 +62,8 @@ SIGNATURES = {
     "bm_pool_put_dense": (i32, [vp, u32, u32, vp, u64, i32]),
     "bm_pool_put_positions": (i32, [vp, u32, u32, vp, vp, i32]),
     "bm_pool_info": (i32, [vp, ctypes.POINTER(bm_pool_info_t)]),
+    "bm_pool_put_rle": (i32, [vp, u32, u32]),
+    "bm_pool_rle_info": (i32, [vp, u32, P64, P64]),
     "bm_pool_bitmap_cardinality": (i32, [vp, u32, P64]),
     "bm_pool_status": (i32, [vp]),
     "bm_pool_set_dense_config": (i32, [vp, ctypes.POINTER(bm_dense_config_t)]),

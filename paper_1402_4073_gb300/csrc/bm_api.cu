@@ -59,6 +59,7 @@ int validate_ids(const bm_pool* p, const uint32_t* ids, uint32_t n, int path) {
         if (ids[k] >= p->capacity) return BM_ERANGE;
         if (path == BM_PATH_DENSE && !p->dense_present[ids[k]]) return BM_ERANGE;
         if (path == BM_PATH_SPARSE && !p->list_present[ids[k]]) return BM_ERANGE;
+        if (path == BM_PATH_RLE && !p->rle_present[ids[k]]) return BM_ERANGE;
         if (path == BM_PATH_AUTO && !p->dense_present[ids[k]] && !p->list_present[ids[k]])
             return BM_ERANGE;
     }
@@ -101,6 +102,23 @@ int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<ui
         a.out = out_words;
         a.card = reinterpret_cast<unsigned long long*>(out_card);
         rc = launch_sparse(a, p->sparse_cfg, p->sm_count, s);
+    } else if (path == BM_PATH_RLE) {
+        RleArgs a{};
+        a.runs = p->d_runs;
+        a.lits = p->d_lits;
+        a.run_begin = p->d_run_begin;
+        a.lit_begin = p->d_lit_begin;
+        a.run_count = p->d_run_count;
+        a.tile_index = p->d_rle_tiles;
+        a.tiles_plus_one = p->rle_tiles + 1;
+        a.words = p->words;
+        a.r_bits = p->r_bits;
+        a.ids = d_ids;
+        a.n = n;
+        a.pred = pred;
+        a.out = out_words;
+        a.card = reinterpret_cast<unsigned long long*>(out_card);
+        rc = launch_rle(a, p->sm_count, s);
     } else {
         DenseArgs a{};
         a.base = p->d_dense;
@@ -154,7 +172,7 @@ int bm_symmetric(bm_pool* p, const uint32_t* ids, uint32_t n, const uint64_t* ta
 int bm_query_run(bm_pool* p, const bm_query* q, uint64_t* out_card, int32_t* chosen_path,
                  void* stream) {
     if (!p || !q || !q->out_words || q->reserved) return BM_EINVAL;
-    if (q->path < BM_PATH_AUTO || q->path > BM_PATH_SPARSE) return BM_EINVAL;
+    if (q->path < BM_PATH_AUTO || q->path > BM_PATH_RLE) return BM_EINVAL;
     std::lock_guard<std::mutex> lk(p->mu);
     int rc = validate_ids(p, q->ids, q->n, q->path);
     if (rc) return rc;

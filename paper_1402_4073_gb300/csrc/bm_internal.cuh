@@ -104,6 +104,42 @@ struct SparseConfig {
 };
 
 int launch_sparse(const SparseArgs& a, const SparseConfig& cfg, int sm_count, cudaStream_t s);
+
+// Word-aligned run-length form of a bitmap (EWAH-like, Sec. 2.1): maximal
+// runs of all-zero words, all-one words or literal words.  A run is a uint2:
+// x = first word | type << 30, y = index of its first literal word among the
+// bitmap's literals (literal runs).  Each bitmap's runs end with a sentinel
+// run starting at word ceil(r/64).
+constexpr uint32_t kRunClean0 = 0, kRunClean1 = 1, kRunLiteral = 2;
+constexpr uint32_t kRunStartMask = (1u << 30) - 1u;
+constexpr uint32_t kRleTileWords = 256;  // words per tile of the run index and kernel
+
+// Arguments of one run-length query launch.
+struct RleArgs {
+    const uint2* runs;            // pool run arena
+    const uint64_t* lits;         // pool literal arena
+    const uint64_t* run_begin;    // device, per id: first run in the arena
+    const uint64_t* lit_begin;    // device, per id: first literal in the arena
+    const uint32_t* run_count;    // device, per id: runs including the sentinel
+    const uint32_t* tile_index;   // device, per id: tiles + 1 summaries: run holding the tile's
+                                  // first word | class << 30 (clean-0 / clean-1 over the whole
+                                  // tile, else literal: to be decoded)
+    uint32_t tiles_plus_one;
+    uint64_t words, r_bits;
+    const uint32_t* ids;
+    uint32_t n;
+    Pred pred;
+    uint64_t* out;
+    unsigned long long* card;
+};
+
+int launch_rle(const RleArgs& a, int sm_count, cudaStream_t s);
+// Run-length encoding of `words` words (host): runs (with the sentinel),
+// literal words, and the summary of every kRleTileWords-word tile (tiles + 1
+// entries): index of the run holding its first word | class << 30, the class
+// being the run's type when that clean run covers the tile, else literal.
+void rle_encode(const uint64_t* words, uint64_t nwords, std::vector<uint2>& runs,
+                std::vector<uint64_t>& lits, std::vector<uint32_t>& tile_index);
 int launch_cardinality(const uint64_t* words, uint64_t r_bits, unsigned long long* out,
                        int sm_count, cudaStream_t s);
 int planes_for(uint32_t n);  // counter planes needed for counts 0..n
@@ -139,6 +175,19 @@ struct bm_pool {
     uint64_t* d_list_begin = nullptr;     // per id, device copy
     uint32_t tiles_per_list = 0;
 
+    // run-length form: growable run and literal arenas, per-id tile index
+    uint2* d_runs = nullptr;
+    uint64_t runs_cap = 0, runs_used = 0;
+    uint64_t* d_lits = nullptr;
+    uint64_t lits_cap = 0, lits_used = 0;
+    uint64_t* d_run_begin = nullptr;      // per id, device
+    uint64_t* d_lit_begin = nullptr;      // per id, device
+    uint32_t* d_run_count = nullptr;      // per id, device
+    uint32_t* d_rle_tiles = nullptr;      // capacity * (rle_tiles + 1)
+    uint32_t rle_tiles = 0;               // ceil(words / kRleTileWords)
+    std::vector<uint8_t> rle_present;
+    std::vector<uint64_t> rle_runs, rle_lits;  // host: per id runs and literal words
+
     int* d_err = nullptr;
     static constexpr int kSlots = 8;
     bm_stage_slot slots[kSlots];
@@ -164,5 +213,6 @@ int stage_acquire(bm_pool* p, size_t bytes, bm_stage_slot** out);
 int stage_commit(bm_stage_slot* slot, size_t bytes, cudaStream_t s);
 int stage_release(bm_stage_slot* slot, cudaStream_t s);
 int track_alloc(bm_pool* p, void** ptr, size_t bytes);
+void track_free(bm_pool* p, void* ptr, size_t bytes);
 void batch_state_free(bm_pool* p);
 }  // namespace bm

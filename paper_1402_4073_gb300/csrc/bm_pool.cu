@@ -28,7 +28,7 @@ int track_alloc(bm_pool* p, void** ptr, size_t bytes) {
     return BM_OK;
 }
 
-static void track_free(bm_pool* p, void* ptr, size_t bytes) {
+void track_free(bm_pool* p, void* ptr, size_t bytes) {
     if (!ptr) return;
     cudaFree(ptr);
     p->device_bytes -= std::min<uint64_t>(p->device_bytes, bytes);
@@ -214,6 +214,10 @@ int bm_pool_create(int device, uint64_t r_bits, uint32_t capacity, uint64_t mem_
     p->list_len.assign(capacity, 0);
     p->list_present.assign(capacity, 0);
     p->tiles_per_list = (uint32_t)((r_bits + kListTileRows - 1) / kListTileRows);
+    p->rle_tiles = (uint32_t)((p->words + kRleTileWords - 1) / kRleTileWords);
+    p->rle_present.assign(capacity, 0);
+    p->rle_runs.assign(capacity, 0);
+    p->rle_lits.assign(capacity, 0);
     *out = p;
     return BM_OK;
 }
@@ -233,6 +237,9 @@ int bm_pool_destroy(bm_pool* p) {
     if (p->d_pos) cudaFree(p->d_pos);
     if (p->d_tile_index) cudaFree(p->d_tile_index);
     if (p->d_list_begin) cudaFree(p->d_list_begin);
+    for (void* q : {(void*)p->d_runs, (void*)p->d_lits, (void*)p->d_run_begin, (void*)p->d_lit_begin,
+                    (void*)p->d_run_count, (void*)p->d_rle_tiles})
+        if (q) cudaFree(q);
     delete p;
     return BM_OK;
 }
@@ -403,6 +410,8 @@ int bm_pool_info(const bm_pool* p, bm_pool_info_t* out) {
     out->capacity = p->capacity;
     out->dense_loaded = (uint32_t)std::count(p->dense_present.begin(), p->dense_present.end(), 1);
     out->lists_loaded = (uint32_t)std::count(p->list_present.begin(), p->list_present.end(), 1);
+    out->rle_loaded = (uint32_t)std::count(p->rle_present.begin(), p->rle_present.end(), 1);
+    out->reserved = 0;
     out->sm_count = (uint32_t)p->sm_count;
     out->device_bytes = p->device_bytes;
     out->dense_base = p->d_dense;

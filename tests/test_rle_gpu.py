@@ -1,0 +1,154 @@
+"""GPU parity of the run-length path (word runs of zeros, ones and literals
+with clean-run pruning) against the CPU oracle on the dense view, bit-exact:
+clustered and scattered inputs, clean inputs of both kinds, ragged r, more
+inputs than one classification pass, and predicates whose transitions fall
+at or below the number of all-ones inputs of a tile."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bm():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1402_4073_gb300 as bm
+    return bm
+
+
+def _run(bm, pool, q, path):
+    out = pool.empty_words()
+    out.fill_(-1)
+    card = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    chosen = bm.query_run(pool, q, out, card, path=path)
+    torch.cuda.synchronize()
+    pool.status()
+    assert chosen == path
+    return bm.to_numpy_words(out), int(card.item())
+
+
+def _runs_of(words: np.ndarray) -> tuple[int, int]:
+    """(runs, literal words) of the word-run form, restated here: maximal runs
+    of equal kind, kinds all-zero / all-one / other."""
+    kind = np.where(words == 0, 0, np.where(words == np.uint64(0xFFFFFFFFFFFFFFFF), 1, 2))
+    runs = 1 + int(np.count_nonzero(kind[1:] != kind[:-1])) if len(kind) else 0
+    return runs, int(np.count_nonzero(kind == 2))
+
+
+def _pool(bm, words, r_bits):
+    pool = bm.Pool(r_bits, words.shape[0])
+    pool.put_dense(words)
+    pool.put_rle()
+    return pool
+
+
+def _mixed_words(dg, r_bits, stream):
+    """Clustered (long runs), scattered, all-zero, all-one and word-alternating
+    bitmaps side by side."""
+    nw = (r_bits + 63) // 64
+    clustered = dg.runs(stream, r_bits, np.array([0.3, 0.05, 0.6, 0.01]), 3000.0)
+    scattered = dg.bernoulli(stream + 1, r_bits, np.array([0.01, 0.5]))
+    zero = np.zeros((1, nw), np.uint64)
+    one = np.full((1, nw), np.uint64(0xFFFFFFFFFFFFFFFF))
+    alt = np.zeros((1, nw), np.uint64)
+    alt[0, ::2] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    alt[0, 1::4] = np.uint64(0x00FF00FF00FF00FF)
+    words = np.concatenate([clustered, scattered, zero, one, alt])
+    tail = r_bits % 64
+    if tail:
+        words[:, -1] &= np.uint64((1 << tail) - 1)
+    return words
+
+
+@pytest.mark.parametrize("r_bits", [64, 100, 16384, 16384 * 3 + 4099, 1 << 20])
+def test_rle_matches_oracle(bm, oracle_lib, dg, r_bits):
+    words = _mixed_words(dg, r_bits, dg.STREAM_TESTS + 20000)
+    n_bm = words.shape[0]
+    with _pool(bm, words, r_bits) as pool:
+        for k in range(n_bm):
+            assert pool.rle_info(k) == _runs_of(words[k]), k
+        ids = np.array([0, 1, 2, 3, 4, 5, 6, 7, 8, 7, 7, 2], dtype=np.uint32)  # ones input thrice
+        n = len(ids)
+        for theta in (0, 1, 2, 3, 4, 5, 7, n, n + 1):
+            q = dg.Query(ids, 0, theta=theta)
+            got = _run(bm, pool, q, bm.PATH_RLE)
+            want = oracle_lib.query(words, q, r_bits)
+            assert np.array_equal(got[0], want[0]) and got[1] == want[1], f"theta={theta}"
+        for lo, hi in ((1, 3), (3, 5), (4, 12)):
+            q = dg.Query(ids, 1, lo=lo, hi=hi)
+            got = _run(bm, pool, q, bm.PATH_RLE)
+            want = oracle_lib.query(words, q, r_bits)
+            assert np.array_equal(got[0], want[0]) and got[1] == want[1], f"[{lo},{hi}]"
+        # many transitions (a table), with f(0) = 1 and odd counts
+        f = (np.arange(n + 1) % 2 == 1)
+        f[0] = True
+        q = dg.Query(ids, 2, table=dg.table_from_bools(f))
+        got = _run(bm, pool, q, bm.PATH_RLE)
+        want = oracle_lib.query(words, q, r_bits)
+        assert np.array_equal(got[0], want[0]) and got[1] == want[1], "table"
+
+
+def test_rle_many_inputs_and_clean_ones(bm, oracle_lib, dg):
+    """n = 2500 (three classification passes of 1024) with a third of the
+    inputs all ones: thresholds below, at and above the clean-one count."""
+    r_bits = 16384 * 5 + 77
+    nw = (r_bits + 63) // 64
+    base = dg.runs(dg.STREAM_TESTS + 20100, r_bits, np.linspace(0.001, 0.7, 60), 2000.0)
+    one = np.full((1, nw), np.uint64(0xFFFFFFFFFFFFFFFF))
+    one[0, -1] &= np.uint64((1 << (r_bits % 64)) - 1)
+    words = np.concatenate([base, one])
+    n = 2500
+    ids = (np.arange(n) % words.shape[0]).astype(np.uint32)
+    ids[::3] = 60  # the all-ones bitmap, 834 times
+    with _pool(bm, words, r_bits) as pool:
+        for theta in (1, 800, 834, 835, 900, 1300, n):
+            q = dg.Query(ids, 0, theta=theta)
+            got = _run(bm, pool, q, bm.PATH_RLE)
+            want = oracle_lib.query(words, q, r_bits)
+            assert np.array_equal(got[0], want[0]) and got[1] == want[1], f"theta={theta}"
+        q = dg.Query(ids, 1, lo=834, hi=860)
+        got = _run(bm, pool, q, bm.PATH_RLE)
+        want = oracle_lib.query(words, q, r_bits)
+        assert np.array_equal(got[0], want[0]) and got[1] == want[1], "interval"
+        # same answers on the dense path
+        dense = _run(bm, pool, q, bm.PATH_DENSE)
+        assert np.array_equal(dense[0], got[0]) and dense[1] == got[1]
+
+
+def test_rle_clustered_workload_subset(bm, oracle_lib, dg):
+    """Scaled clustered workload: 64 bitmaps of r = 2^22 rows, densities
+    max(0.5/k, 1e-4) in runs of mean 4096 rows; the four bench queries."""
+    r_bits = 1 << 22
+    words = dg.runs(dg.STREAM_TESTS + 20200, r_bits, dg.config2_density(64), 4096.0)
+    ids = np.arange(64, dtype=np.uint32)
+    with _pool(bm, words, r_bits) as pool:
+        for q in (dg.Query(ids, 0, theta=2), dg.Query(ids, 0, theta=32), dg.Query(ids, 0, theta=63),
+                  dg.Query(ids, 1, lo=2, hi=10)):
+            got = _run(bm, pool, q, bm.PATH_RLE)
+            want = oracle_lib.query(words, q, r_bits)
+            assert np.array_equal(got[0], want[0]) and got[1] == want[1], q
+
+
+def test_rle_errors(bm, dg):
+    r_bits = 5000
+    words = dg.bernoulli(dg.STREAM_TESTS + 20300, r_bits, np.array([0.1, 0.2, 0.3]))
+    with bm.Pool(r_bits, 4) as pool:
+        pool.put_dense(words)
+        with pytest.raises(bm.BMError) as e:
+            pool.put_rle(0, 4)  # id 3 has no dense copy
+        assert e.value.code == bm.BM_ERANGE
+        pool.put_rle(0, 3)
+        assert pool.info()["rle_loaded"] == 3
+        out = pool.empty_words()
+        with pytest.raises(bm.BMError) as e:  # id 3 has no run-length form
+            bm.query_run(pool, dg.Query(np.array([0, 3]), 0, theta=1), out, path=bm.PATH_RLE)
+        assert e.value.code == bm.BM_ERANGE
+        with pytest.raises(bm.BMError) as e:  # single queries only
+            bm.threshold_batch(pool, [dg.Query(np.array([0, 1]), 0, theta=1)], [out],
+                               torch.zeros(1, dtype=torch.int64, device="cuda"), paths=[bm.PATH_RLE])
+        assert e.value.code == bm.BM_EINVAL
+        with pytest.raises(bm.BMError):
+            pool.rle_info(3)
