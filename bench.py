@@ -329,12 +329,74 @@ def bench_sparse(bm, datagen, reps: int = 20, small: bool = False, config: str =
                      "frac": round(alg / us / 1e3 / peak, 4)})
     pool.status()
     pool.close()
+    cos = bench_cosparse(bm, datagen, r_bits, nbm, reps, peak, config)
     return {"workload": f"sparse single queries: {nbm} x 2^{r_bits.bit_length() - 1} pool "
                         "(densities log-uniform [1e-5,1e-2], position lists), theta=min(N,8)",
             "kernel": "ScanCount (scancount_kernel)", "bytes": "4 * positions + r/8 per query",
             "peak": peak, "peak_source": f"hbm_gbs of {peak_src}",
             "timing": f"median of {reps} launches, CUDA events around each bm_query_run",
-            "queries": rows, "autotune": tune}
+            "queries": rows, "autotune": tune, "co_sparse": cos}
+
+
+def bench_cosparse(bm, datagen, r_bits, nbm, reps, peak, config=""):
+    """Co-sparse pool: half the bitmaps of density d, half of density 1 - d
+    (d log-uniform [1e-5,1e-2]); the dense half loaded as lists of their zeros
+    (complement identity, Sec. 2.3).  Random queries of N = 1500, 537, 128,
+    16 ids, theta = N/2 + 1, on ScanCount and on the dense path."""
+    import numpy as np
+    import torch
+    half = nbm // 2
+    d = datagen.pool_densities(datagen.STREAM_SPARSE + (11 << 32), nbm, 1e-5, 1e-2)
+    d[half:] = 1.0 - d[half:]
+    words = datagen.bernoulli(datagen.STREAM_SPARSE + (12 << 32), r_bits, d)
+    flat1, offs1 = datagen.positions(words[:half], r_bits)
+    comp = ~words[half:]
+    if r_bits % 64:
+        comp[:, -1] &= np.uint64((1 << (r_bits % 64)) - 1)
+    flat0, offs0 = datagen.positions(comp, r_bits)
+    del comp
+    pool = bm.Pool(r_bits, nbm)
+    pool.put_dense(words)
+    del words
+    pool.put_positions(flat1, offs1)
+    pool.put_positions(flat0, offs0, first_id=half, zeros=True)
+    if config:
+        pool.set_sparse_config(*[int(x) for x in config.split(",")])
+    else:
+        pool.autotune()
+    lens = np.concatenate([offs1[1:].astype(np.int64) - offs1[:-1].astype(np.int64),
+                           offs0[1:].astype(np.int64) - offs0[:-1].astype(np.int64)])
+    del flat1, flat0
+    out = pool.empty_words()
+    card = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = []
+    for n in (1500, 537, 128, 16):
+        ids = datagen.floyd(datagen.STREAM_SPARSE + (13 << 32) + n, nbm, n)
+        q = datagen.Query(ids, datagen.KIND_THRESHOLD, theta=n // 2 + 1)
+        t = {}
+        for path in (bm.PATH_SPARSE, bm.PATH_DENSE):
+            pq = bm.PreparedQuery(pool, q, out, path)
+            for _ in range(3):
+                pq.run(card)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+            torch.cuda.synchronize()
+            for i in range(reps):
+                ev[2 * i].record(stream)
+                pq.run(card)
+                ev[2 * i + 1].record(stream)
+            torch.cuda.synchronize()
+            t[path] = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(reps)) * 1e3
+        b = int(lens[ids].sum())
+        alg = 4 * b + r_bits // 8
+        rows.append({"N": n, "inputs_by_zeros": int((ids >= half).sum()), "listed_positions": b,
+                     "sparse_us": round(t[bm.PATH_SPARSE], 1), "dense_us": round(t[bm.PATH_DENSE], 1),
+                     "sparse_frac": round(alg / t[bm.PATH_SPARSE] / 1e3 / peak, 4)})
+    pool.status()
+    pool.close()
+    return {"workload": f"co-sparse: {nbm} x 2^{r_bits.bit_length() - 1} pool, half of density d, "
+                        "half 1 - d (d log-uniform [1e-5,1e-2]) given by their zeros; theta = N/2 + 1",
+            "queries": rows}
 
 
 def bench_rle(bm, datagen, reps: int = 10, small: bool = False):

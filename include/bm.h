@@ -109,6 +109,21 @@ int bm_pool_put_positions(bm_pool* pool, uint32_t first_id, uint32_t count,
                           int positions_on_device);
 
 /*
+ * As bm_pool_put_positions, but list j holds the rows where bitmap j is 0
+ * (the complement's positions): the sparse path can then take a dense input
+ * through its few zeros.  By the complement identity (Sec. 2.3: NOT T(theta,
+ * b) = T(N - theta + 1, NOT b), read input by input), a query with D such
+ * inputs starts every ScanCount counter at D and subtracts one per listed
+ * zero, so each counter still ends at the number of inputs holding its row;
+ * results are identical on every path.  A bitmap without a dense copy gets
+ * cardinality r - (list length).  Same arguments and errors as
+ * bm_pool_put_positions.
+ */
+int bm_pool_put_complement_positions(bm_pool* pool, uint32_t first_id, uint32_t count,
+                                     const uint32_t* positions, const uint64_t* offsets,
+                                     int positions_on_device);
+
+/*
  * Build the run-length form of ids first_id .. first_id + count - 1 from their
  * dense copies (which must be loaded; BM_ERANGE otherwise): the word-aligned
  * run form of a compressed bitmap (Sec. 2.1, EWAH), i.e. maximal runs of

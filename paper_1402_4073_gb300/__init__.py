@@ -114,17 +114,18 @@ class Pool:
         check(lib.bm_pool_put_dense(self.handle, first_id, w.shape[0], w.ctypes.data, w.shape[1], 0),
               "bm_pool_put_dense")
 
-    def put_positions(self, flat, offsets, first_id: int = 0):
-        """Load sorted position lists: list j is flat[offsets[j]:offsets[j+1]]."""
+    def put_positions(self, flat, offsets, first_id: int = 0, zeros: bool = False):
+        """Load sorted position lists: list j is flat[offsets[j]:offsets[j+1]],
+        the rows where bitmap first_id + j is 1 (zeros=True: where it is 0)."""
         offs = _host_u64(offsets)
+        fn = lib.bm_pool_put_complement_positions if zeros else lib.bm_pool_put_positions
         if isinstance(flat, torch.Tensor):
-            check(lib.bm_pool_put_positions(self.handle, first_id, len(offs) - 1, flat.data_ptr(),
-                                            offs.ctypes.data, 1 if flat.is_cuda else 0),
-                  "bm_pool_put_positions")
+            check(fn(self.handle, first_id, len(offs) - 1, flat.data_ptr(), offs.ctypes.data,
+                     1 if flat.is_cuda else 0), "bm_pool_put_positions")
             return
         f = _host_u32(flat)
         fp = f.ctypes.data if len(f) else None
-        check(lib.bm_pool_put_positions(self.handle, first_id, len(offs) - 1, fp, offs.ctypes.data, 0),
+        check(fn(self.handle, first_id, len(offs) - 1, fp, offs.ctypes.data, 0),
               "bm_pool_put_positions")
 
     def put_rle(self, first_id: int = 0, count: int | None = None) -> None:

@@ -61,6 +61,7 @@ SIGNATURES = {
     "bm_pool_destroy": (i32, [vp]),
     "bm_pool_put_dense": (i32, [vp, u32, u32, vp, u64, i32]),
     "bm_pool_put_positions": (i32, [vp, u32, u32, vp, vp, i32]),
+    "bm_pool_put_complement_positions": (i32, [vp, u32, u32, vp, vp, i32]),
     "bm_pool_info": (i32, [vp, ctypes.POINTER(bm_pool_info_t)]),
     "bm_pool_put_rle": (i32, [vp, u32, u32]),
     "bm_pool_rle_info": (i32, [vp, u32, P64, P64]),

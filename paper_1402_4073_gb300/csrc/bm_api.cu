@@ -66,6 +66,12 @@ int validate_ids(const bm_pool* p, const uint32_t* ids, uint32_t n, int path) {
     return BM_OK;
 }
 
+uint32_t complement_inputs(const bm_pool* p, const uint32_t* ids, uint32_t n) {
+    uint32_t d = 0;
+    for (uint32_t k = 0; k < n; ++k) d += p->list_complement[ids[k]];
+    return d;
+}
+
 // Stage ids (and a table-mode truth table) and launch the chosen kernel.
 int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<uint8_t>& f,
                int path, uint32_t tile_rows, uint64_t* out_words, uint64_t* out_card,
@@ -98,6 +104,7 @@ int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<ui
         a.r_bits = p->r_bits;
         a.ids = d_ids;
         a.n = n;
+        a.d_fill = complement_inputs(p, ids, n);
         a.pred = pred;
         a.out = out_words;
         a.card = reinterpret_cast<unsigned long long*>(out_card);

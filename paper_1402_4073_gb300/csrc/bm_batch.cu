@@ -36,6 +36,8 @@ struct QueryDesc {
     uint32_t n;
     uint32_t tile_rows;
     uint64_t* out;
+    uint32_t d_fill;  // sparse: inputs given by their zeros (ScanCount counters start here)
+    uint32_t pad;
     Pred pred;
 };
 
@@ -135,7 +137,8 @@ __device__ __forceinline__ unsigned long long sparse_item(const QueryDesc* d, co
                                          reinterpret_cast<const uint4*>(pa.positions),
                                          pa.list_begin, pa.tile_index, pa.tiles_per_list, t0, t1,
                                          (uint32_t)rlo, (uint32_t)(rhi - rlo),
-                                         cnt_words * kPer);  // spares past every item's counters
+                                         cnt_words * kPer,  // spares past every item's counters
+                                         d->d_fill);
     __syncthreads();
     const uint32_t lanes = (uint32_t)((rhi - rlo + 31) / 32);
     uint32_t* out32 = reinterpret_cast<uint32_t*>(d->out);
@@ -574,6 +577,8 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
         hd[i].n = q[i].n;
         hd[i].tile_rows = cand[i].tile_rows;
         hd[i].out = q[i].out_words;
+        hd[i].d_fill = cand[i].path == BM_PATH_SPARSE ? complement_inputs(p, q[i].ids, q[i].n) : 0u;
+        hd[i].pad = 0;
         hd[i].pred = preds[i];
         if (preds[i].mode == 2) {
             uint32_t* t = htab + tab_pos;

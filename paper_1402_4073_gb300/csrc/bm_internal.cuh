@@ -24,6 +24,10 @@ namespace bm {
 
 // Rows covered by one entry of a position list's tile index.
 constexpr uint32_t kListTileRows = 8192;
+// Bit of a list's device begin offset marking a list of zeros (the rows where
+// the bitmap is 0): ScanCount subtracts its positions from counters that
+// start at the number of such inputs (Sec. 2.3, the complement identity).
+constexpr uint64_t kListComplement = 1ull << 63;
 // Most threshold transitions a predicate evaluates as comparators before it
 // switches to a per-row table lookup.
 constexpr int kMaxTransitions = 8;
@@ -84,13 +88,14 @@ int launch_dense(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaS
 // Arguments of one sparse (ScanCount) query launch.
 struct SparseArgs {
     const uint32_t* positions;   // pool list arena
-    const uint64_t* list_begin;  // device, per id: first entry in the arena
+    const uint64_t* list_begin;  // device, per id: first entry in the arena (| kListComplement)
     const uint32_t* tile_index;  // device, per id: tiles_per_list + 1 entries
     uint32_t tiles_per_list;     // ceil(r / kListTileRows)
     uint32_t tile_rows;          // rows per CTA tile, a multiple of kListTileRows
     uint64_t r_bits;
     const uint32_t* ids;         // device, n ids
     uint32_t n;
+    uint32_t d_fill;             // inputs given by their zeros: the counters' start value
     Pred pred;
     uint64_t* out;
     unsigned long long* card;
@@ -171,6 +176,7 @@ struct bm_pool {
     uint64_t pos_cap = 0, pos_used = 0;
     std::vector<uint64_t> list_begin, list_len;  // host, per id
     std::vector<uint8_t> list_present;
+    std::vector<uint8_t> list_complement;  // the list holds the zeros of the bitmap
     uint32_t* d_tile_index = nullptr;     // capacity * tiles_per_list (+1)
     uint64_t* d_list_begin = nullptr;     // per id, device copy
     uint32_t tiles_per_list = 0;
@@ -207,6 +213,8 @@ namespace bm {
 int query_truth(const bm_query* q, std::vector<uint8_t>& f);
 // Host validation of ids for a path (BM_PATH_*).
 int validate_ids(const bm_pool* p, const uint32_t* ids, uint32_t n, int path);
+// Inputs of ids[0..n) whose position list holds their zeros (with repeats).
+uint32_t complement_inputs(const bm_pool* p, const uint32_t* ids, uint32_t n);
 // Reserve a staging slot of at least `bytes`, waiting for its previous use.
 int stage_acquire(bm_pool* p, size_t bytes, bm_stage_slot** out);
 // Copy the slot's first `bytes` to the device on `s` and mark its reuse point.

@@ -213,6 +213,7 @@ int bm_pool_create(int device, uint64_t r_bits, uint32_t capacity, uint64_t mem_
     p->list_begin.assign(capacity, 0);
     p->list_len.assign(capacity, 0);
     p->list_present.assign(capacity, 0);
+    p->list_complement.assign(capacity, 0);
     p->tiles_per_list = (uint32_t)((r_bits + kListTileRows - 1) / kListTileRows);
     p->rle_tiles = (uint32_t)((p->words + kRleTileWords - 1) / kRleTileWords);
     p->rle_present.assign(capacity, 0);
@@ -277,8 +278,11 @@ int bm_pool_put_dense(bm_pool* p, uint32_t first_id, uint32_t count, const uint6
     return BM_OK;
 }
 
-int bm_pool_put_positions(bm_pool* p, uint32_t first_id, uint32_t count, const uint32_t* positions,
-                          const uint64_t* offsets, int on_device) {
+// Lists of ones (complement = false) or of zeros (complement = true): the
+// arena placement, tile index and checks are the same; a list of zeros is
+// marked by bit 63 of its device begin offset.
+static int put_lists(bm_pool* p, uint32_t first_id, uint32_t count, const uint32_t* positions,
+                     const uint64_t* offsets, int on_device, bool complement) {
     if (!p || !offsets || count == 0) return BM_EINVAL;
     if ((uint64_t)first_id + count > p->capacity) return BM_ERANGE;
     const uint64_t total = offsets[count] - offsets[0];
@@ -393,13 +397,26 @@ int bm_pool_put_positions(bm_pool* p, uint32_t first_id, uint32_t count, const u
         p->list_begin[first_id + j] = b;
         p->list_len[first_id + j] = len;
         p->list_present[first_id + j] = 1;
-        if (!p->dense_present[first_id + j]) p->card[first_id + j] = len;
+        p->list_complement[first_id + j] = complement ? 1 : 0;
+        if (!p->dense_present[first_id + j]) p->card[first_id + j] = complement ? p->r_bits - len : len;
+        if (complement) dst_off[j] |= kListComplement;
     }
     BM_CUDA_TRY(cudaMemcpy(p->d_list_begin + first_id, dst_off.data(), (size_t)count * 8,
                            cudaMemcpyHostToDevice));
     BM_CUDA_TRY(cudaDeviceSynchronize());
     p->pos_used += padded;
     return BM_OK;
+}
+
+int bm_pool_put_positions(bm_pool* p, uint32_t first_id, uint32_t count, const uint32_t* positions,
+                          const uint64_t* offsets, int on_device) {
+    return put_lists(p, first_id, count, positions, offsets, on_device, false);
+}
+
+int bm_pool_put_complement_positions(bm_pool* p, uint32_t first_id, uint32_t count,
+                                     const uint32_t* positions, const uint64_t* offsets,
+                                     int on_device) {
+    return put_lists(p, first_id, count, positions, offsets, on_device, true);
 }
 
 int bm_pool_info(const bm_pool* p, bm_pool_info_t* out) {

@@ -30,43 +30,56 @@ constexpr uint32_t kScanWarpWords = 64;  // shared words per warp: a group's sli
 // shared words the helper needs besides the counters (up to 32 warps)
 constexpr uint32_t kScanSmemWords = kScanWarpWords * 32;
 
-// Add the four entries of a vector that lie in rows [lo, lo + nrows).  An
-// entry outside the range (alignment or padding of a slice) goes to the
-// lane's own spare counter word past the tile instead, so the four atomics
-// are issued without branches; the spare words are never read.
+// Add (sub: subtract) one for each of the four entries of a vector that lie
+// in rows [lo, lo + nrows).  An entry outside the range (alignment or padding
+// of a slice) goes to the lane's own spare counter word past the tile
+// instead, so the four atomics are issued without branches; the spare words
+// are never read.  A subtraction never borrows across packed counters: a row
+// is decremented at most once per input given by its zeros, and its counter
+// started at the number of such inputs.
 template <int BITS>
 __device__ __forceinline__ void count_vec(uint32_t* cnt, const uint4& x, uint32_t lo,
-                                          uint32_t nrows, uint32_t spare_row) {
+                                          uint32_t nrows, uint32_t spare_row, bool sub) {
     constexpr uint32_t kPer = 32 / BITS;
     const uint32_t e[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         uint32_t row = e[i] - lo;
         row = row < nrows ? row : spare_row;
-        atomicAdd(&cnt[row / kPer], 1u << (BITS * (row % kPer)));
+        const uint32_t inc = 1u << (BITS * (row % kPer));
+        atomicAdd(&cnt[row / kPer], sub ? 0u - inc : inc);
     }
 }
 
-// Add every position of rows [lo, lo + nrows) of lists ids[0..n) into
-// BITS-bit counters cnt (packed 32 / BITS per word; cnt_rows / (32 / BITS)
-// words for rows, then 32 spare words).  t0, t1: tile-index entries bounding
-// the tile.  vpos: the pool's list arena as 16-byte vectors.  scratch:
-// kScanWarpWords shared words per warp.  s_next: a shared word.  Every
-// thread of the block calls this; it begins with a block barrier.
+// Count rows [lo, lo + nrows) of lists ids[0..n) into BITS-bit counters cnt
+// (packed 32 / BITS per word; cnt_rows / (32 / BITS) words for rows, then 32
+// spare words), which hold zero on entry: every position of a list of ones
+// adds one; the counters first take d_fill, the number of inputs given by a
+// list of their zeros, and every position of such a list subtracts one, so
+// each counter ends at the number of inputs holding its row (the complement
+// identity of Sec. 2.3 applied input by input).  t0, t1: tile-index entries
+// bounding the tile.  vpos: the pool's list arena as 16-byte vectors.
+// scratch: kScanWarpWords shared words per warp.  s_next: a shared word.
+// Every thread of the block calls this; it begins with a block barrier.
 template <int BITS, int U>
 __device__ __forceinline__ void count_tile(uint32_t* cnt, uint32_t* scratch, uint32_t* s_next,
                                            const uint32_t* ids, uint32_t n, const uint4* vpos,
                                            const uint64_t* list_begin,
                                            const uint32_t* tile_index, uint32_t tiles_per_list,
                                            uint64_t t0, uint64_t t1, uint32_t lo,
-                                           uint32_t nrows, uint32_t cnt_rows) {
+                                           uint32_t nrows, uint32_t cnt_rows, uint32_t d_fill) {
     constexpr uint32_t kFull = 0xFFFFFFFFu;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t le = (2u << lane) - 1u, lt = (1u << lane) - 1u;
     const uint32_t spare = cnt_rows + lane * (32 / BITS);  // this lane's spare counter word
     const uint32_t ngroups = (n + 31) / 32;
-    uint32_t* ws = scratch + warp * kScanWarpWords;  // [0,32): first vector, [32,64): offset
+    uint32_t* ws = scratch + warp * kScanWarpWords;  // [0,32): first vector | zeros bit, [32,64): offset
     if (threadIdx.x == 0) *s_next = nw;
+    if (d_fill) {  // the rows' counters (those evaluated) start at d_fill
+        const uint32_t fill = BITS == 8 ? d_fill * 0x01010101u : d_fill * 0x00010001u;
+        const uint32_t words = (nrows + 31) / 32 * BITS;  // BITS words per 32 rows
+        for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) cnt[i] = fill;
+    }
     __syncthreads();
     // slice of list 32 g + lane: first vector vs, vectors nv (0: empty)
     auto bounds = [&](uint32_t g, uint32_t& vs, uint32_t& nv) {
@@ -77,9 +90,11 @@ __device__ __forceinline__ void count_tile(uint32_t* cnt, uint32_t* scratch, uin
             const uint32_t id = __ldg(ids + j);
             const uint32_t* idx = tile_index + (uint64_t)id * (tiles_per_list + 1);
             const uint32_t b = __ldg(idx + t0), en = __ldg(idx + t1);
-            const uint64_t base = __ldg(list_begin + id);
+            const uint64_t begin = __ldg(list_begin + id);
+            const uint64_t base = begin & ~kListComplement;
             vs = (uint32_t)((base + b) >> 2);
             nv = b < en ? (uint32_t)((base + en + 3) >> 2) - vs : 0u;
+            vs |= (uint32_t)(begin >> 32) & 0x80000000u;  // bit 31: a list of zeros
         }
     };
     // With fewer groups than warps, a team of `team` warps shares each group,
@@ -115,7 +130,8 @@ __device__ __forceinline__ void count_tile(uint32_t* cnt, uint32_t* scratch, uin
         const uint32_t member = u % team;
         // this warp's pieces: member + k * team, k = 0, 1, ...
         const uint32_t mine = pieces > member ? (pieces - member + team - 1) / team : 0u;
-        auto fetch = [&](uint32_t k0, uint4 (&x)[U]) {
+        auto fetch = [&](uint32_t k0, uint4 (&x)[U], uint32_t& subs) {
+            subs = 0u;
 #pragma unroll
             for (int i = 0; i < U; ++i) {
                 const uint32_t q = member + (k0 + i) * team;
@@ -127,22 +143,27 @@ __device__ __forceinline__ void count_tile(uint32_t* cnt, uint32_t* scratch, uin
                         kFull, (nv != 0u && (start >> 5) == q) ? (1u << (start & 31)) : 0u);
                     const uint32_t r = before + __popc(inside & le) - 1u;
                     const uint32_t v = q * 32 + lane;
-                    if (v < total) x[i] = ld_stream(vpos + ws[r] + (v - ws[32 + r]));
+                    if (v < total) {
+                        const uint32_t first = ws[r];
+                        x[i] = ld_stream(vpos + (first & 0x7FFFFFFFu) + (v - ws[32 + r]));
+                        subs |= (first >> 31) << i;
+                    }
                 }
             }
         };
-        auto add = [&](const uint4 (&x)[U]) {
+        auto add = [&](const uint4 (&x)[U], uint32_t subs) {
 #pragma unroll
-            for (int i = 0; i < U; ++i) count_vec<BITS>(cnt, x[i], lo, nrows, spare);
+            for (int i = 0; i < U; ++i) count_vec<BITS>(cnt, x[i], lo, nrows, spare, (subs >> i) & 1u);
         };
         uint4 xa[U], xb[U];
-        fetch(0, xa);
+        uint32_t sa, sb;
+        fetch(0, xa, sa);
         for (uint32_t k0 = 0; k0 < mine; k0 += 2 * U) {
-            if (k0 + U < mine) fetch(k0 + U, xb);
-            add(xa);
+            if (k0 + U < mine) fetch(k0 + U, xb, sb);
+            add(xa, sa);
             if (k0 + U >= mine) break;
-            if (k0 + 2 * U < mine) fetch(k0 + 2 * U, xa);
-            add(xb);
+            if (k0 + 2 * U < mine) fetch(k0 + 2 * U, xa, sa);
+            add(xb, sb);
         }
         __syncwarp();  // the group's slices are read before the next unit writes them
         u = un;

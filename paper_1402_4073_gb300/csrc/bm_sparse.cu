@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(512, 2) scancount_kernel(SparseArgs a) {
         count_tile<BITS, U>(cnt, scratch, &s_next, a.ids, a.n,
                             reinterpret_cast<const uint4*>(a.positions),
                             a.list_begin, a.tile_index, a.tiles_per_list, t0, t1, (uint32_t)lo,
-                            (uint32_t)(hi - lo), a.tile_rows);
+                            (uint32_t)(hi - lo), a.tile_rows, a.d_fill);
         __syncthreads();
         // 32 rows per thread -> one 32-bit output lane
         const uint32_t lanes = (uint32_t)((hi - lo + 31) / 32);

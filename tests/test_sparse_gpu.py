@@ -194,6 +194,61 @@ def test_list_padding_and_alignment(bm, oracle_lib, dg, tile):
             assert np.array_equal(got[0], words[k]) and got[1] == len(lists[k]), k
 
 
+def _zeros_of(words: np.ndarray, r_bits: int) -> np.ndarray:
+    comp = ~words
+    if r_bits % 64:
+        comp[:, -1] &= np.uint64((1 << (r_bits % 64)) - 1)
+    return comp
+
+
+@pytest.mark.parametrize("tile", [8192, 32768, 65536])
+@pytest.mark.parametrize("r_bits", [70001, (1 << 18) + 3])
+def test_lists_of_zeros(bm, oracle_lib, dg, tile, r_bits):
+    """Dense inputs given to ScanCount by their zeros (the complement
+    identity, input by input), mixed with inputs given by their ones, in
+    single and batched queries, with 8- and 16-bit counters: every result
+    equals the oracle on the dense view."""
+    lo_d = dg.log_uniform(dg.uniform(dg.STREAM_TESTS + 11500, 30), 1e-4, 0.1)
+    hi_d = 1.0 - dg.log_uniform(dg.uniform(dg.STREAM_TESTS + 11501, 30), 1e-4, 0.1)
+    words = dg.bernoulli(dg.STREAM_TESTS + 11502, r_bits, np.concatenate([lo_d, hi_d]))
+    nw = words.shape[1]
+    ones = np.full((1, nw), np.uint64(0xFFFFFFFFFFFFFFFF))
+    ones[0, -1] = np.uint64((1 << (r_bits % 64)) - 1) if r_bits % 64 else ones[0, -1]
+    words = np.concatenate([words, ones])  # id 60: all ones (an empty list of zeros)
+    words[:, 17] |= np.uint64(0xF0)        # rows every input holds
+    flat1, offs1 = dg.positions(words[:30], r_bits)
+    flat0, offs0 = dg.positions(_zeros_of(words[30:], r_bits), r_bits)
+    n_bm = words.shape[0]
+    with bm.Pool(r_bits, n_bm) as pool:
+        pool.put_dense(words)
+        pool.put_positions(flat1, offs1)
+        pool.put_positions(flat0, offs0, first_id=30, zeros=True)
+        pool.set_sparse_config(tile, 512, 2)
+        for k in (0, 29, 30, 59, 60):
+            assert pool.bitmap_cardinality(k) == oracle_lib.cardinality(words[k], r_bits)
+        small = np.array([0, 31, 5, 60, 45, 45, 12, 59, 2, 33], dtype=np.uint32)
+        big = (np.arange(400) * 7 % n_bm).astype(np.uint32)  # 16-bit counters, repeats
+        queries = []
+        for ids in (small, big):
+            n = len(ids)
+            for theta in (1, 2, n // 3, n // 2, n - 1, n):
+                queries.append(dg.Query(ids, 0, theta=theta))
+            queries.append(dg.Query(ids, 1, lo=n // 4, hi=n // 2))
+            f = (np.arange(n + 1) % 3 == 0)
+            queries.append(dg.Query(ids, 2, table=dg.table_from_bools(f)))
+        wants = [oracle_lib.query(words, q, r_bits) for q in queries]
+        for q, want in zip(queries, wants):
+            got, _ = _run(bm, pool, q, bm.PATH_SPARSE)
+            _eq(got, want, f"n={q.n} kind={q.kind} theta={q.theta}")
+        outs = [pool.empty_words().fill_(-1) for _ in queries]
+        cards = torch.full((len(queries),), -1, dtype=torch.int64, device="cuda")
+        bm.threshold_batch(pool, queries, outs, cards, paths=[bm.PATH_SPARSE] * len(queries))
+        torch.cuda.synchronize()
+        pool.status()
+        for i, want in enumerate(wants):
+            _eq((bm.to_numpy_words(outs[i]), int(cards[i].item())), want, f"batch query {i}")
+
+
 def test_lists_from_device_and_validation(bm, dg):
     r_bits = 50000
     words = dg.bernoulli(dg.STREAM_TESTS + 11300, r_bits, np.array([0.01, 0.02, 0.03]))
