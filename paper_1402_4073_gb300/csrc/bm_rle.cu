@@ -8,15 +8,18 @@
 // thread).  For every input it reads one summary word of the tile (the run
 // holding the tile's first word, and whether that clean run covers the whole
 // tile).  An input that is one clean run over the whole tile costs nothing
-// more: a clean-0 run is skipped, a
-// clean-1 run adds one to a per-tile constant c1.  The other inputs are
-// decoded, a half-warp per input, into a shared-memory stage of 16 tile-wide
-// words (clean runs filled, literal words copied from the literal arena),
-// and each thread adds its column of the stage into K counter planes with the
-// sideways-sum blocks of the dense kernel.  The predicate is then evaluated
-// on count + c1: thresholds move down by c1, a table is shifted by c1.  Only
-// the runs and literal words of the tile are read from HBM, never the clean
-// words themselves.
+// more: a clean-0 run is skipped, a clean-1 run adds one to a per-tile
+// constant c1.  The other inputs are decoded, a half-warp per input, 16 at a
+// time: their clean-0 runs add nothing, their clean-1 runs add one to the
+// coverage of the columns they span (a difference array, two shared-memory
+// updates per run), and only their literal words go to a shared stage, with
+// one mask bit per (column, input).  Each thread then adds its column's
+// literal words into K counter planes (the sixteen-input sideways-sum block
+// of the dense kernel when all sixteen are literal, else two at a time), and
+// at the end of the tile evaluates the predicate on count + c1 + coverage of
+// its column: thresholds move down by that offset, a table is read past it.
+// Only the runs and literal words of the tile are read from HBM, and clean
+// words cost neither stores nor additions.
 #include <algorithm>
 #include <vector>
 
@@ -67,17 +70,20 @@ constexpr uint32_t kRleGroup = 2 * kRleThreads / 32;  // inputs staged per round
 constexpr uint32_t kRleChunk = 1024;             // inputs classified per pass
 
 // Decode words [w0, w1) of one input (runs from index r0 of the input's runs)
-// into dst[0 .. w1 - w0) with the 16 lanes of a half-warp, so that a warp
-// decodes two inputs at once.  The lanes read 16 runs at a time; each lane
-// writes the words of its own run when the run's part of the tile is short,
-// and the half-warp then writes the long ones together, each long run's words
-// spread over its lanes.
+// with the 16 lanes of a half-warp, so that a warp decodes two inputs at
+// once.  Clean-0 runs add nothing; a clean-1 run adds one to the coverage of
+// its columns (two updates of the difference array cov); a literal word w is
+// stored at dst[w - w0] with bit `slot` of lmask[w - w0] set.  The lanes read
+// 16 runs at a time; a lane handles its own run when the run's part of the
+// tile is short, and the half-warp then spreads the long literal runs.
 __device__ __forceinline__ void decode_tile(const RleArgs& a, uint32_t id, uint32_t r0,
                                             uint32_t w0, uint32_t w1, uint64_t* dst,
+                                            uint32_t slot, uint32_t* lmask, int* cov,
                                             uint32_t lane) {
-    constexpr uint32_t kShort = 8;  // words a lane writes alone
+    constexpr uint32_t kShort = 8;  // literal words a lane stores alone
     const uint32_t seg = lane & 15, half = lane >> 4;
     const uint32_t hmask = 0xFFFFu << (16 * half);
+    const uint32_t bit = 1u << slot;
     const uint2* runs = a.runs + __ldg(a.run_begin + id);
     const uint64_t* lits = a.lits + __ldg(a.lit_begin + id);
     const uint32_t nruns = __ldg(a.run_count + id);  // including the sentinel
@@ -92,29 +98,28 @@ __device__ __forceinline__ void decode_tile(const RleArgs& a, uint32_t id, uint3
         }
         const uint32_t b = max(st, w0), e = min(nx, w1);  // this run's words in the tile
         const bool live = st < w1;
-        const bool lone = live && e - b <= kShort;
-        if (lone) {
-            if (type == kRunLiteral) {
-                for (uint32_t w = b; w < e; ++w) dst[w - w0] = __ldg(lits + lo + (w - st));
-            } else {
-                const uint64_t fill = type == kRunClean1 ? ~0ull : 0ull;
-                for (uint32_t w = b; w < e; ++w) dst[w - w0] = fill;
+        if (live && type == kRunClean1) {
+            atomicAdd(&cov[b - w0], 1);
+            atomicAdd(&cov[e - w0], -1);
+        }
+        const bool lit = live && type == kRunLiteral;
+        if (lit && e - b <= kShort) {
+            for (uint32_t w = b; w < e; ++w) {
+                dst[w - w0] = __ldg(lits + lo + (w - st));
+                atomicOr(&lmask[w - w0], bit);
             }
         }
-        uint32_t big = (__ballot_sync(hmask, live && !lone) >> (16 * half)) & 0xFFFFu;
+        uint32_t big = (__ballot_sync(hmask, lit && e - b > kShort) >> (16 * half)) & 0xFFFFu;
         while (big) {
             const uint32_t j = __ffs(big) - 1;
             big &= big - 1;
             const uint32_t sj = __shfl_sync(hmask, st, j, 16);
             const uint32_t bj = __shfl_sync(hmask, b, j, 16);
             const uint32_t ej = __shfl_sync(hmask, e, j, 16);
-            const uint32_t tj = __shfl_sync(hmask, type, j, 16);
             const uint32_t lj = __shfl_sync(hmask, lo, j, 16);
-            if (tj == kRunLiteral) {
-                for (uint32_t w = bj + seg; w < ej; w += 16) dst[w - w0] = __ldg(lits + lj + (w - sj));
-            } else {
-                const uint64_t fill = tj == kRunClean1 ? ~0ull : 0ull;
-                for (uint32_t w = bj + seg; w < ej; w += 16) dst[w - w0] = fill;
+            for (uint32_t w = bj + seg; w < ej; w += 16) {
+                dst[w - w0] = __ldg(lits + lj + (w - sj));
+                atomicOr(&lmask[w - w0], bit);
             }
         }
         // runs start in increasing order: once one starts past the tile, all later do
@@ -122,34 +127,41 @@ __device__ __forceinline__ void decode_tile(const RleArgs& a, uint32_t id, uint3
     }
 }
 
-// The predicate on count + c1, as a predicate on the count: transitions at
-// or below c1 always hold (folded into v0), the rest move down by c1; a
-// table is shifted by c1 into `tab` (shared, tab_words words).
-__device__ __forceinline__ Pred shift_pred(const Pred& p, uint32_t c1, uint32_t* tab,
-                                           uint32_t tab_words) {
+// Output word of one column: the predicate on count + off per row, where the
+// planes P hold the literal words' count and `off` the inputs covering the
+// column with ones (c1 + clean-1 coverage).  Thresholds move down by off
+// (those at or below it always hold); a table is read at count + off.
+template <int K>
+__device__ __forceinline__ uint64_t eval_offset(const uint32_t (&P)[2][K], const Pred& p,
+                                                const uint32_t* tab, uint32_t off) {
+    if (p.mode == 2) {
+        uint64_t word = 0;
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+            for (int b = 0; b < 32; ++b) {
+                uint32_t c = 0;
+#pragma unroll
+                for (int j = 0; j < K; ++j) c |= ((P[l][j] >> b) & 1u) << j;
+                c += off;
+                word |= (uint64_t)((tab[c >> 5] >> (c & 31u)) & 1u) << (32 * l + b);
+            }
+        return word;
+    }
     Pred q = p;
     if (p.mode == 1) {
         uint32_t k = 0;
 #pragma unroll
         for (int i = 0; i < kMaxTransitions; ++i) {
             if ((uint32_t)i < p.ntrans) {
-                if (p.trans[i] <= c1)
+                if (p.trans[i] <= off)
                     q.v0 ^= 1u;
                 else
-                    q.trans[k++] = p.trans[i] - c1;
+                    q.trans[k++] = p.trans[i] - off;
             }
         }
         q.ntrans = k;
-    } else if (p.mode == 2) {
-        // bit c of the shifted table = bit c + c1 of f (bits past n read as 0)
-        const uint32_t sw = c1 / 32, sb = c1 % 32;
-        for (uint32_t w = threadIdx.x; w < tab_words; w += blockDim.x) {
-            const uint32_t lo = sw + w < p.table_words32 ? p.table[sw + w] : 0u;
-            const uint32_t hi = sw + w + 1 < p.table_words32 ? p.table[sw + w + 1] : 0u;
-            tab[w] = sb ? (lo >> sb) | (hi << (32 - sb)) : lo;
-        }
     }
-    return q;
+    return (uint64_t)eval_pred<K>(P[0], q, tab) | ((uint64_t)eval_pred<K>(P[1], q, tab) << 32);
 }
 
 template <int K>
@@ -157,10 +169,15 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2) rle_kernel(RleAr
     extern __shared__ __align__(16) uint64_t sm64[];
     uint64_t* stage = sm64;                                                    // [kRleGroup][256]
     uint2* dirty = reinterpret_cast<uint2*>(stage + kRleGroup * kRleThreads);  // [kRleChunk]
-    uint32_t* tab = reinterpret_cast<uint32_t*>(dirty + kRleChunk);           // shifted table
+    uint32_t* tab = reinterpret_cast<uint32_t*>(dirty + kRleChunk);           // f over 0..n
     __shared__ uint32_t s_c1, s_nd;
+    __shared__ uint32_t lmask[kRleThreads];  // per column: staged inputs with a literal word
+    __shared__ int cov[kRleThreads + 1];     // clean-1 coverage, as differences
+    __shared__ int warp_tot[kRleThreads / 32];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t tab_words = a.pred.mode == 2 ? (a.n + 1 + 31) / 32 : 0u;
+    for (uint32_t w = tid; w < tab_words; w += kRleThreads) tab[w] = a.pred.table[w];
+    lmask[tid] = 0u;
     const uint64_t ntiles = (a.words + kRleTileWords - 1) / kRleTileWords;
     unsigned long long card = 0;
     // ids and tile summaries of up to four inputs per thread.  With one chunk
@@ -194,7 +211,11 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2) rle_kernel(RleAr
         const uint32_t w1 = (uint32_t)min((uint64_t)w0 + kRleTileWords, a.words);
         uint32_t P[2][K];
         zero_planes<K, 2>(P);
-        if (tid == 0) s_c1 = 0u;
+        if (tid == 0) {
+            s_c1 = 0u;
+            cov[kRleThreads] = 0;
+        }
+        cov[tid] = 0;
         for (uint32_t c0 = 0; c0 < a.n; c0 += kRleChunk) {
             const uint32_t m = min(kRleChunk, a.n - c0);
             if (tid == 0) s_nd = 0u;
@@ -222,38 +243,69 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2) rle_kernel(RleAr
             __syncthreads();  // every thread has nd before the next chunk resets it
             for (uint32_t g0 = 0; g0 < nd; g0 += kRleGroup) {
                 const uint32_t gn = min(kRleGroup, nd - g0);
-                // half-warp h of the CTA decodes entry h of the group
+                // half-warp h of the CTA decodes entry h of the group into stage row h
                 const uint32_t e = 2 * warp + (lane >> 4);
                 if (e < gn) {
                     const uint2 d = dirty[g0 + e];
-                    decode_tile(a, d.x, d.y, w0, w1, stage + e * kRleThreads, lane);
+                    decode_tile(a, d.x, d.y, w0, w1, stage + e * kRleThreads, e, lmask, cov, lane);
                 }
                 __syncthreads();
-                auto get = [&](uint32_t b) {
-                    const uint64_t x = stage[b * kRleThreads + tid];
-                    Slice<2> s;
-                    s.v[0] = (uint32_t)x;
-                    s.v[1] = (uint32_t)(x >> 32);
-                    return s;
+                // add this column's literal words: a full group through the
+                // sixteen-input tree, otherwise two at a time
+                uint32_t mk = lmask[tid];
+                lmask[tid] = 0u;
+                auto get = [&](uint32_t row) {
+                    const uint64_t x = stage[row * kRleThreads + tid];
+                    Slice<2> v;
+                    v.v[0] = (uint32_t)x;
+                    v.v[1] = (uint32_t)(x >> 32);
+                    return v;
                 };
-                if (gn == kRleGroup) {
+                if (mk == 0xFFFFu) {
                     Slice<2> v[16];
 #pragma unroll
-                    for (int b = 0; b < 16; ++b) v[b] = get(b);
+                    for (int i = 0; i < 16; ++i) v[i] = get(i);
                     add_group<K, 2, 16>(P, v);
                 } else {
-                    add_partial<K, 2>(P, gn, get);
+                    while (mk) {
+                        const uint32_t i0 = __ffs(mk) - 1;
+                        mk &= mk - 1;
+                        const Slice<2> u = get(i0);
+                        if (mk) {
+                            const uint32_t i1 = __ffs(mk) - 1;
+                            mk &= mk - 1;
+                            const Slice<2> v = get(i1);
+                            add2<K>(P[0], u.v[0], v.v[0]);
+                            add2<K>(P[1], u.v[1], v.v[1]);
+                        } else {
+                            add1<K>(P[0], u.v[0]);
+                            add1<K>(P[1], u.v[1]);
+                        }
+                    }
                 }
                 __syncthreads();
             }
         }
-        __syncthreads();  // c1 is final
-        const Pred pr = shift_pred(a.pred, s_c1, tab, tab_words);
-        if (a.pred.mode == 2) __syncthreads();
+        __syncthreads();  // c1 and the coverage differences are final
+        // coverage of this thread's column: inclusive prefix sum of cov
+        int x = cov[tid];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        for (uint32_t w = 0; w < warp; ++w) x += warp_tot[w];
+        const uint32_t off = s_c1 + (uint32_t)x;
         const uint64_t col = (uint64_t)w0 + tid;
-        if (col < a.words)
-            card += finish_column<K, 2>(P, pr, tab, a.r_bits, a.words, a.out, col, false);
-        __syncthreads();  // s_c1, s_nd and tab are reused by the next tile
+        if (col < a.words) {
+            uint64_t word = eval_offset<K>(P, a.pred, tab, off);
+            if (col == a.words - 1 && (a.r_bits & 63u)) word &= (1ull << (a.r_bits & 63u)) - 1ull;
+            a.out[col] = word;
+            card += (unsigned long long)__popcll(word);
+        }
+        __syncthreads();  // s_c1, s_nd, cov and warp_tot are reused by the next tile
     }
     flush_card(card, a.card);
 }
