@@ -6,7 +6,8 @@ its Python binding) never imports, loads or calls anything here, and nothing
 here imports the product.
 
 ``oracle.c`` is the plain definition of a threshold / symmetric-function query
-over bitmaps (per-row counters, then a comparison), compiled with gcc.
+over bitmaps (per-row counters, then a comparison) and of a weighted threshold
+with an optional AND / OR / AND NOT of one more bitmap, compiled with gcc.
 ``mlp.py`` is the fp64 NumPy statement of the selector network's forward pass,
 backward pass and Adam step.
 """
@@ -50,6 +51,8 @@ def _L():
         lib.oracle_symmetric.restype = None
         lib.oracle_scancount.argtypes = [vp, vp, vp, u32, u64, u64, vp, u64, u64, vp, vp]
         lib.oracle_scancount.restype = None
+        lib.oracle_weighted.argtypes = [vp, u64, vp, vp, u32, u64, u64, u32, vp, u64, u64, vp, vp]
+        lib.oracle_weighted.restype = None
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = None
         lib.oracle_get_threads.argtypes = []
@@ -146,6 +149,25 @@ def scancount(flat: np.ndarray, offsets: np.ndarray, ids, r_bits: int, theta: in
     fp = flat if len(flat) else np.zeros(1, dtype=np.uint32)
     _L().oracle_scancount(_p(fp), _p(offsets), _p(ids), len(ids), r_bits, int(theta),
                           _p(table), w0, w1, _p(out), _p(card))
+    return out[: w1 - w0], int(card[0])
+
+
+def weighted(pool: np.ndarray, ids, weights, r_bits: int, theta: int, post_op: int = 0,
+             post: np.ndarray | None = None, w0: int = 0, w1: int | None = None):
+    """(output words, ones) of the weighted threshold [sum of weights of the
+    inputs holding a row >= theta], combined with `post` by post_op (0 none,
+    1 AND, 2 OR, 3 AND NOT)."""
+    pool, ids = _prep(pool, ids)
+    weights = np.ascontiguousarray(np.asarray(weights, dtype=np.uint32))
+    assert len(weights) == len(ids)
+    w1 = _words(r_bits) if w1 is None else w1
+    if post is None:
+        post = np.zeros(_words(r_bits), dtype=np.uint64)
+    post = np.ascontiguousarray(post, dtype=np.uint64)
+    out = np.zeros(max(w1 - w0, 1), dtype=np.uint64)
+    card = np.zeros(1, dtype=np.uint64)
+    _L().oracle_weighted(_p(pool), pool.shape[1], _p(ids), _p(weights), len(ids), r_bits,
+                         int(theta), int(post_op), _p(post), w0, w1, _p(out), _p(card))
     return out[: w1 - w0], int(card[0])
 
 

@@ -11,6 +11,10 @@
  *   threshold query:      output bit i = [c_i >= theta]
  *   symmetric query:      output bit i = f(c_i), f given as bits 0..N
  *   cardinality:          number of ones in the output bitmap
+ *   weighted threshold:   output bit i = [sum of weights[k] over inputs k
+ *                         holding row i >= theta] (Sec. 2.3: a weight is the
+ *                         number of copies of an input), then optionally
+ *                         combined with one more bitmap by AND, OR or AND NOT
  *
  * A repeated id counts once per repeat (the paper's weighting by replication,
  * Sec. 2.3).  Rows >= r are never set in the output and input bits at rows
@@ -160,5 +164,43 @@ void oracle_scancount(const uint32_t *positions, const uint64_t *offsets, const 
         }
     }
     free(counts);
+    *card = total;
+}
+
+/*
+ * Weighted threshold (Sec. 2.3) with an optional combining step: for each row
+ * i < r, w_i = sum of weights[k] over inputs k whose bit i is 1 (64-bit sum);
+ * t_i = [w_i >= theta]; then out_i = t_i (post_op 0), t_i AND m_i (1),
+ * t_i OR m_i (2) or t_i AND NOT m_i (3), m being the bitmap `post` (ignored
+ * for post_op 0).  Output words w0..w1-1 and their number of ones.
+ */
+void oracle_weighted(const uint64_t *base, uint64_t stride_words, const uint32_t *ids,
+                     const uint32_t *weights, uint32_t n, uint64_t r_bits, uint64_t theta,
+                     uint32_t post_op, const uint64_t *post, uint64_t w0, uint64_t w1,
+                     uint64_t *out, uint64_t *card) {
+    uint64_t total = 0;
+#pragma omp parallel for schedule(static) reduction(+ : total)
+    for (int64_t w = (int64_t)w0; w < (int64_t)w1; ++w) {
+        uint64_t word = 0;
+        for (int b = 0; b < 64; ++b) {
+            uint64_t i = (uint64_t)w * 64 + (uint64_t)b;
+            if (i >= r_bits) continue;
+            uint64_t sum = 0;
+            for (uint32_t k = 0; k < n; ++k)
+                if (oracle_bit(base + (uint64_t)ids[k] * stride_words, i)) sum += weights[k];
+            int t = sum >= theta;
+            if (post_op != 0) {
+                int m = oracle_bit(post, i);
+                if (post_op == 1) t = t && m;
+                else if (post_op == 2) t = t || m;
+                else t = t && !m;
+            }
+            if (t) {
+                word |= (uint64_t)1 << b;
+                total += 1;
+            }
+        }
+        out[(uint64_t)w - w0] = word;
+    }
     *card = total;
 }

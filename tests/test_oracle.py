@@ -269,6 +269,56 @@ def test_monotone_permutation_duplicates(oracle_lib, dg):
     assert np.array_equal(got, pool[0] & pool[1] & _mask(r_bits))
 
 
+# --- weighted thresholds and combining (Sec. 2.3) -------------------------------
+
+
+def test_weighted_is_replication(oracle_lib, dg):
+    """A weight is the number of copies of an input (Sec. 2.3)."""
+    r_bits = 3000
+    pool = _rand_pool(dg, 6, r_bits, 0.4, stream=30)
+    ids = np.array([0, 1, 2, 3, 4, 5])
+    weights = np.array([1, 3, 2, 5, 1, 4])
+    rep = np.repeat(ids, weights)
+    for theta in range(0, int(weights.sum()) + 2):
+        a = oracle_lib.weighted(pool, ids, weights, r_bits, theta)
+        b = oracle_lib.threshold(pool, rep, r_bits, theta)
+        assert np.array_equal(a[0], b[0]) and a[1] == b[1], theta
+    # weight 0 drops an input; all weights 1 is the plain threshold
+    a = oracle_lib.weighted(pool, ids, [1, 0, 1, 0, 1, 0], r_bits, 2)
+    assert np.array_equal(a[0], oracle_lib.threshold(pool, [0, 2, 4], r_bits, 2)[0])
+    a = oracle_lib.weighted(pool, ids, np.ones(6), r_bits, 3)
+    assert np.array_equal(a[0], oracle_lib.threshold(pool, ids, r_bits, 3)[0])
+
+
+def test_weighted_binary_weights_exhaustive(oracle_lib):
+    """Inputs k = 0..N-1 with bit(k, i) = bit k of i and weight 2^k: every row's
+    weighted sum is i itself, so the output is [i >= theta] exactly."""
+    N = 10
+    pool, r_bits = _exhaustive_pool(N)
+    weights = 1 << np.arange(N)
+    for theta in (0, 1, 2, 3, 511, 512, 513, 1000, 1023, 1024):
+        out, card = oracle_lib.weighted(pool, np.arange(N), weights, r_bits, theta)
+        assert card == max(0, r_bits - theta)
+        got = np.unpackbits(out.view(np.uint8), bitorder="little")[:r_bits].astype(bool)
+        assert np.array_equal(got, np.arange(r_bits) >= theta)
+    # large weights: one input of weight 2^31 decides alone
+    out, _ = oracle_lib.weighted(pool, [3, 0, 1], [1 << 31, 1, 1], r_bits, 1 << 31)
+    assert np.array_equal(out, pool[3] & _mask(r_bits))
+
+
+def test_weighted_post_ops(oracle_lib, dg):
+    r_bits = 777
+    pool = _rand_pool(dg, 5, r_bits, 0.5, stream=31)
+    ids, weights = [0, 1, 2, 3], [2, 1, 1, 3]
+    t, _ = oracle_lib.weighted(pool, ids, weights, r_bits, 3)
+    m = pool[4]
+    mask = _mask(r_bits)
+    for op, want in ((1, t & m), (2, (t | m) & mask), (3, t & ~m & mask)):
+        got, card = oracle_lib.weighted(pool, ids, weights, r_bits, 3, op, m)
+        assert np.array_equal(got, want), op
+        assert card == int(sum(bin(int(x)).count("1") for x in want))
+
+
 # --- independent formulations from the paper -----------------------------------
 
 
