@@ -470,6 +470,59 @@ def bench_rle(bm, datagen, reps: int = 10, small: bool = False):
             "pools": pools}
 
 
+def bench_weighted(bm, datagen, reps: int = 5, small: bool = False):
+    """Weighted thresholds (Sec. 2.3) on the main benchmark's pool (N = 256 bitmaps of
+    r = 2^26 rows): weights uniform in [1, wmax] for wmax = 4, 1000 and 2^20, theta =
+    sum / 8, alone and ANDed with bitmap 0; for wmax = 4 also the same query as
+    replicated ids through the dense threshold.  small: r = 2^22."""
+    import numpy as np
+    import torch
+    r_bits, n = ((1 << 22) if small else (1 << 26)), 256
+    words, _ = datagen.config2(r_bits, n)
+    pool = bm.Pool(r_bits, n)
+    pool.put_dense(words)
+    del words
+    pool.set_dense_config(0, 256, 4, 2, 2, 2)
+    ids = np.arange(n, dtype=np.uint32)
+    out = pool.empty_words()
+    card = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        torch.cuda.synchronize()
+        for i in range(reps):
+            ev[2 * i].record(stream)
+            fn()
+            ev[2 * i + 1].record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(reps)) * 1e3
+
+    rows = []
+    for wmax in (4, 1000, 1 << 20):
+        u = datagen.uniform(datagen.STREAM_TESTS + 777, n)
+        w = np.maximum(1, (u * wmax).astype(np.int64)).astype(np.uint32)
+        total = int(w.astype(np.uint64).sum())
+        theta = total // 8
+        row = {"wmax": wmax, "sum": total, "theta": theta,
+               "weighted_us": round(timed(lambda: bm.weighted_threshold(pool, ids, w, theta, out, card)), 1),
+               "weighted_and_us": round(timed(lambda: bm.weighted_threshold(pool, ids, w, theta, out, card,
+                                                                            bm.POST_AND, 0)), 1)}
+        if total <= bm.BM_N_MAX:
+            rep = np.repeat(ids, w)
+            row["replicated_ids_us"] = round(timed(lambda: bm.threshold(pool, rep, theta, out, card)), 1)
+        row["input_GBps"] = round(query_bytes(n, r_bits) / row["weighted_us"] / 1e3, 1)
+        rows.append(row)
+    pool.status()
+    pool.close()
+    return {"workload": f"weighted: the main pool (N={n} x r=2^{r_bits.bit_length() - 1}), "
+                        "weights uniform in [1, wmax], theta = sum/8",
+            "kernel": "weighted_kernel (bit-sliced weighted add)",
+            "timing": f"median of {reps} calls, CUDA events", "queries": rows}
+
+
 def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds: float = 0.8,
                   small: bool = False):
     """Serving loop on the 10,000 x 2^22 pool: Poisson arrivals at each
@@ -570,8 +623,8 @@ def main():
                     help="rows = 2^r_log2 (smaller cases are for profiling only)")
     ap.add_argument("--dense-config", default="",
                     help="variant,threads,stages,ctas_per_sm[,adder]: skip the variant search")
-    ap.add_argument("--parts", default="dense,sparse,rle,batch,selector,serving",
-                    help="comma list of dense, sparse, rle, batch, selector, serving")
+    ap.add_argument("--parts", default="dense,sparse,rle,weighted,batch,selector,serving",
+                    help="comma list of dense, sparse, rle, weighted, batch, selector, serving")
     ap.add_argument("--sparse-config", default="",
                     help="tile_rows,threads,ctas_per_sm,unroll for the sparse part: skip tuning")
     ap.add_argument("--small", action="store_true",
@@ -700,6 +753,8 @@ def main():
         extra["sparse"] = bench_sparse(bm, datagen, small=args.small, config=args.sparse_config)
     if "rle" in parts:
         extra["rle"] = bench_rle(bm, datagen, small=args.small)
+    if "weighted" in parts:
+        extra["weighted"] = bench_weighted(bm, datagen, small=args.small)
     if "batch" in parts:
         extra["batched"] = bench_batched(bm, datagen, small=args.small)
     if "selector" in parts:

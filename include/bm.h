@@ -310,6 +310,40 @@ int bm_threshold_batch(bm_pool* pool, const bm_query* q, uint32_t nq, uint64_t* 
                        int32_t* chosen_paths, void* stream);
 
 /*
+ * Weighted threshold with an optional combining step (Sec. 2.3: a weight is
+ * a number of copies of an input; the result of a threshold is again a
+ * bitmap, Sec. 1).  Row i of the output is selected iff
+ *     sum over k of weights[k] * (bit i of bitmap ids[k])  >=  theta,
+ * and is then combined with the pool bitmap post_id: unchanged
+ * (BM_POST_NONE), AND, OR or AND NOT (result AND NOT bitmap), in the same
+ * pass.  theta = 0 selects every row; theta above the sum of the weights
+ * selects none.  Each input is read once whatever its weight (dense path).
+ * weights[k] <= BM_WEIGHT_MAX, sum of the weights < 2^32; weight 0 drops an
+ * input.  out_card: device uint64 or NULL.  Errors: BM_EINVAL (null pointer,
+ * n > BM_N_MAX, a weight or sum out of range, bad post_op, reserved != 0),
+ * BM_ERANGE (an id or post_id without a dense bitmap), BM_ECUDA.
+ */
+#define BM_POST_NONE 0u
+#define BM_POST_AND 1u
+#define BM_POST_OR 2u
+#define BM_POST_ANDNOT 3u
+#define BM_WEIGHT_MAX 16777215u /* 2^24 - 1 */
+
+typedef struct bm_weighted_query {
+    const uint32_t* ids;      /* host, n pool ids (repeats allowed) */
+    const uint32_t* weights;  /* host, n weights */
+    uint32_t n;               /* 0 .. BM_N_MAX */
+    uint32_t post_op;         /* BM_POST_* */
+    uint64_t theta;
+    uint32_t post_id;         /* the combined bitmap (post_op != BM_POST_NONE) */
+    uint32_t reserved;        /* must be 0 */
+    uint64_t* out_words;      /* device, ceil(r/64) words, written in full */
+} bm_weighted_query;
+
+int bm_weighted_threshold(bm_pool* pool, const bm_weighted_query* q, uint64_t* out_card,
+                          void* stream);
+
+/*
  * Number of ones among the first r_bits rows of a device bitmap `words`
  * (ceil(r/64) words), written to the device uint64 *out_card (Sec. 2.1: the
  * cardinality of the set a bitmap stores).  Asynchronous on `stream`.

@@ -23,6 +23,7 @@ lib = _native.load()
 BM_OK, BM_EINVAL, BM_ERANGE, BM_ENOMEM, BM_ECUDA, BM_ETIMEOUT, BM_EBUSY, BM_ENOTREADY = (
     0, -1, -2, -3, -4, -5, -6, -7)
 BM_N_MAX = 65535
+BM_WEIGHT_MAX = (1 << 24) - 1
 
 
 class BMError(RuntimeError):
@@ -326,6 +327,26 @@ def threshold_batch(pool: Pool, queries, outs, out_cards: torch.Tensor, paths=No
     """Run a batch of queries (objects with ids, kind, theta, lo, hi, table)
     into outs[i]; cardinalities into out_cards[i].  Returns the chosen paths."""
     return PreparedBatch(pool, queries, outs, paths).run(out_cards, stream).copy()
+
+
+POST_NONE, POST_AND, POST_OR, POST_ANDNOT = 0, 1, 2, 3
+
+
+def weighted_threshold(pool: Pool, ids, weights, theta: int, out_words: torch.Tensor,
+                       out_card: torch.Tensor | None = None, post_op: int = POST_NONE,
+                       post_id: int = 0, stream=None) -> None:
+    """Rows where the sum of weights of the inputs holding them reaches theta,
+    optionally ANDed / ORed / AND-NOTed with pool bitmap post_id."""
+    if out_words.numel() * out_words.element_size() < 8 * pool.words:
+        raise ValueError("output buffer too small")
+    i = _host_u32(ids)
+    w = _host_u32(weights)
+    if len(i) != len(w):
+        raise ValueError("ids and weights differ in length")
+    q = _native.bm_weighted_query(i.ctypes.data if len(i) else None, w.ctypes.data if len(w) else None,
+                                  len(i), post_op, theta, post_id, 0, out_words.data_ptr())
+    check(lib.bm_weighted_threshold(pool.handle, ctypes.byref(q), _dev_ptr(out_card, 8),
+                                    _stream(stream)), "bm_weighted_threshold")
 
 
 def query_features(pool: Pool, query) -> np.ndarray:

@@ -22,6 +22,11 @@ class bm_query(ctypes.Structure):
                 ("table", vp), ("out_words", vp), ("path", ctypes.c_int32), ("reserved", u32)]
 
 
+class bm_weighted_query(ctypes.Structure):
+    _fields_ = [("ids", vp), ("weights", vp), ("n", u32), ("post_op", u32), ("theta", u64),
+                ("post_id", u32), ("reserved", u32), ("out_words", vp)]
+
+
 class bm_pool_info_t(ctypes.Structure):
     _fields_ = [("r_bits", u64), ("words", u64), ("stride_words", u64), ("capacity", u32),
                 ("dense_loaded", u32), ("lists_loaded", u32), ("sm_count", u32),
@@ -64,6 +69,7 @@ SIGNATURES = {
     "bm_pool_put_complement_positions": (i32, [vp, u32, u32, vp, vp, i32]),
     "bm_pool_info": (i32, [vp, ctypes.POINTER(bm_pool_info_t)]),
     "bm_pool_put_rle": (i32, [vp, u32, u32]),
+    "bm_weighted_threshold": (i32, [vp, ctypes.POINTER(bm_weighted_query), vp, vp]),
     "bm_pool_rle_info": (i32, [vp, u32, P64, P64]),
     "bm_pool_bitmap_cardinality": (i32, [vp, u32, P64]),
     "bm_pool_status": (i32, [vp]),

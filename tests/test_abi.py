@@ -50,3 +50,21 @@ def test_product_never_imports_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "oracle.c" not in text, f
+
+
+def test_binding_constants_match_header():
+    """Every #define of include/bm.h that the binding mirrors has its value."""
+    import re
+
+    import paper_1402_4073_gb300 as bm
+    text = open(os.path.join(ROOT, "include", "bm.h")).read()
+    defs = {m.group(1): int(m.group(2), 0)
+            for m in re.finditer(r"#define\s+(BM_\w+)\s+\(?(-?(?:0x[0-9a-fA-F]+|\d+))u?\)?", text)}
+    mirrored = {"BM_N_MAX": bm.BM_N_MAX, "BM_WEIGHT_MAX": bm.BM_WEIGHT_MAX,
+                "BM_PATH_AUTO": bm.PATH_AUTO, "BM_PATH_DENSE": bm.PATH_DENSE,
+                "BM_PATH_SPARSE": bm.PATH_SPARSE, "BM_PATH_RLE": bm.PATH_RLE,
+                "BM_POST_NONE": bm.POST_NONE, "BM_POST_AND": bm.POST_AND,
+                "BM_POST_OR": bm.POST_OR, "BM_POST_ANDNOT": bm.POST_ANDNOT,
+                "BM_EINVAL": bm.BM_EINVAL, "BM_ERANGE": bm.BM_ERANGE}
+    for name, value in mirrored.items():
+        assert defs.get(name) == value, (name, defs.get(name), value)
