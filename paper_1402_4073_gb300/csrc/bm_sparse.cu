@@ -7,11 +7,11 @@
 // width switch by N, packed four or two to a 32-bit word and incremented
 // with shared-memory atomics).  The tile's slice of a list comes from the
 // pool's per-list tile index (first entry at every multiple of 8192 rows), so
-// a list is never searched; the slices of up to 1024 lists are laid end to
-// end as one stream of 16-byte vectors and read by all lanes at once
+// a list is never searched; warps take groups of 32 lists and read their
+// slices, laid end to end, as one stream of 16-byte vectors
 // (bm_scan_common.cuh).  Then each thread turns 32 counters into one 32-bit
-// output lane through the truth table of f held in shared memory, stores it
-// and popcounts it.
+// output lane (a plain threshold by SIMD compares, any other f through its
+// truth table in shared memory), stores it and popcounts it.
 #include <algorithm>
 
 #include "bm_scan_common.cuh"
