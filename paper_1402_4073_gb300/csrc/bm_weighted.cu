@@ -5,13 +5,15 @@
 // the result may then be ANDed, ORed or AND-NOTed with one more bitmap of the
 // pool in the same pass (the result of a threshold is again a bitmap, Sec. 1).
 //
-// GPU form: a thread owns one 64-bit word column and keeps K counter planes
-// (the bits of the weighted sum of its 64 rows) in registers.  Inputs of
+// GPU form: a thread owns a column of one or two 64-bit words and keeps K
+// counter planes (the bits of the weighted sum of its rows) in registers.  Inputs of
 // weight 1 go through the sixteen-input sideways-sum blocks of the dense
 // kernel.  An input of weight w > 1 is added once per set bit j of w, at plane
 // j, by rippling its word upwards (half adders); the warp stops a ripple as
-// soon as no lane carries.  The predicate is the runtime comparator of the
-// dense kernel against theta - 1.
+// soon as no lane carries.  When the weights are small (their sum at most 8
+// per input and within BM_N_MAX) they are expanded into copies instead, which
+// the sideways-sum blocks add faster than ripples.  The predicate is the
+// runtime comparator of the dense kernel against theta - 1.
 #include <algorithm>
 #include <vector>
 
@@ -53,53 +55,66 @@ __device__ __forceinline__ void add_at(uint32_t (&P)[K], uint32_t c, uint32_t j)
     }
 }
 
-template <int K>
+// L = 4: a thread owns two 64-bit words (128 rows, 16-byte loads); L = 2: one.
+template <int K, int L>
 __global__ void __launch_bounds__(256) weighted_kernel(WeightedArgs a) {
+    constexpr uint32_t W = L / 2;  // words per thread
+    const uint64_t ncols = (a.words + W - 1) / W;
     for (uint64_t col = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;; col += (uint64_t)gridDim.x * blockDim.x) {
         // the whole warp stays in the loop while any lane has a column (ripples vote)
-        if (!__any_sync(0xFFFFFFFFu, col < a.words)) break;
-        const bool mine = col < a.words;
-        const uint64_t c = mine ? col : a.words - 1;  // idle lanes reread a valid column
-        uint32_t P[2][K];
-        zero_planes<K, 2>(P);
-        count_column<K, 16, 2>(P, a.base + c, a.ids1, a.n1, a.stride_words);
+        if (!__any_sync(0xFFFFFFFFu, col < ncols)) break;
+        const bool mine = col < ncols;
+        const uint64_t c = mine ? col : ncols - 1;  // idle lanes reread a valid column
+        const uint64_t w0 = W * c;                  // first word of the column
+        uint32_t P[L][K];
+        zero_planes<K, L>(P);
+        count_column<K, 16, L>(P, a.base + w0, a.ids1, a.n1, a.stride_words);
         // weighted inputs, the next one's word in flight while this one ripples
-        Slice<2> x_next;
-        if (a.nw) x_next = ld_slice<2>(a.base + (uint64_t)__ldg(a.idsw) * a.stride_words + c);
+        Slice<L> x_next;
+        if (a.nw) x_next = ld_slice<L>(a.base + (uint64_t)__ldg(a.idsw) * a.stride_words + w0);
         for (uint32_t k = 0; k < a.nw; ++k) {
-            const Slice<2> x = x_next;
+            const Slice<L> x = x_next;
             uint32_t w = __ldg(a.wts + k);
             if (k + 1 < a.nw)
-                x_next = ld_slice<2>(a.base + (uint64_t)__ldg(a.idsw + k + 1) * a.stride_words + c);
+                x_next = ld_slice<L>(a.base + (uint64_t)__ldg(a.idsw + k + 1) * a.stride_words + w0);
             while (w) {
                 const uint32_t j = __ffs(w) - 1;
                 w &= w - 1;
-                add_at<K>(P[0], x.v[0], j);
-                add_at<K>(P[1], x.v[1], j);
+#pragma unroll
+                for (int l = 0; l < L; ++l) add_at<K>(P[l], x.v[l], j);
             }
         }
-        uint64_t word = a.all ? ~0ull
-                              : ((uint64_t)greater_than<K>(P[0], (uint32_t)(a.theta - 1)) |
-                                 ((uint64_t)greater_than<K>(P[1], (uint32_t)(a.theta - 1)) << 32));
-        if (a.post_op) {
-            const uint64_t m = __ldg(a.post + c);
-            word = a.post_op == BM_POST_AND ? (word & m) : a.post_op == BM_POST_OR ? (word | m) : (word & ~m);
+        unsigned long long ones = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < W; ++i) {
+            const uint64_t wi = w0 + i;
+            uint64_t word = a.all ? ~0ull
+                                  : ((uint64_t)greater_than<K>(P[2 * i], (uint32_t)(a.theta - 1)) |
+                                     ((uint64_t)greater_than<K>(P[2 * i + 1], (uint32_t)(a.theta - 1)) << 32));
+            if (wi < a.words) {
+                if (a.post_op) {
+                    const uint64_t m = __ldg(a.post + wi);
+                    word = a.post_op == BM_POST_AND ? (word & m)
+                         : a.post_op == BM_POST_OR  ? (word | m)
+                                                    : (word & ~m);
+                }
+                if (wi == a.words - 1 && (a.r_bits & 63u)) word &= (1ull << (a.r_bits & 63u)) - 1ull;
+                if (mine) {
+                    a.out[wi] = word;
+                    ones += (unsigned long long)__popcll(word);
+                }
+            }
         }
-        if (c == a.words - 1 && (a.r_bits & 63u)) word &= (1ull << (a.r_bits & 63u)) - 1ull;
-        unsigned long long n1s = 0;
-        if (mine) {
-            a.out[c] = word;
-            n1s = (unsigned long long)__popcll(word);
-        }
-        flush_card(n1s, a.card);
+        flush_card(ones, a.card);
     }
 }
 
-template <int K>
+template <int K, int L>
 int launch_k(const WeightedArgs& a, int sm_count, cudaStream_t s) {
-    const uint64_t blocks = (a.words + 255) / 256;
+    const uint64_t cols = (a.words + L / 2 - 1) / (L / 2);
+    const uint64_t blocks = (cols + 255) / 256;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(blocks, (uint64_t)sm_count * 4));
-    weighted_kernel<K><<<grid, 256, 0, s>>>(a);
+    weighted_kernel<K, L><<<grid, 256, 0, s>>>(a);
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
 }
@@ -132,6 +147,15 @@ extern "C" int bm_weighted_threshold(bm_pool* p, const bm_weighted_query* q, uin
         }
     }
     if (sum > 0xFFFFFFFFull) return BM_EINVAL;
+    // small weights: as many copies as the weight (Sec. 2.3's own reading),
+    // all through the sideways-sum blocks; the copies of an input sit side by
+    // side, so its repeated reads come from the caches
+    if (!idsw.empty() && sum <= BM_N_MAX && sum <= 8ull * q->n) {
+        ids1.clear();
+        for (uint32_t k = 0; k < q->n; ++k) ids1.insert(ids1.end(), q->weights[k], q->ids[k]);
+        idsw.clear();
+        wts.clear();
+    }
     BM_CUDA_TRY(cudaSetDevice(p->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // staging: weight-1 ids (16-byte aligned), weighted ids, weights
@@ -177,16 +201,17 @@ extern "C" int bm_weighted_threshold(bm_pool* p, const bm_weighted_query* q, uin
         while (planes < 32 && (sum >> planes) != 0) ++planes;
     }
     if (p->words) {
+        // two words per thread while the planes of both fit in registers
         if (planes <= 8)
-            rc = launch_k<8>(a, p->sm_count, s);
+            rc = launch_k<8, 4>(a, p->sm_count, s);
         else if (planes <= 12)
-            rc = launch_k<12>(a, p->sm_count, s);
+            rc = launch_k<12, 4>(a, p->sm_count, s);
         else if (planes <= 16)
-            rc = launch_k<16>(a, p->sm_count, s);
+            rc = launch_k<16, 2>(a, p->sm_count, s);
         else if (planes <= 24)
-            rc = launch_k<24>(a, p->sm_count, s);
+            rc = launch_k<24, 2>(a, p->sm_count, s);
         else
-            rc = launch_k<32>(a, p->sm_count, s);
+            rc = launch_k<32, 2>(a, p->sm_count, s);
     }
     int rc2 = stage_release(sl, s);
     return rc ? rc : rc2;
