@@ -1,6 +1,8 @@
 """Parity at the full workload sizes, in the configurations bench.py times:
 the mixed batch (2000 x 2^24, 4096 queries), the sparse + selector pool
-(5000 x 2^24, dense and lists) and the serving pool (10000 x 2^22).  The
+(5000 x 2^24, dense and lists), the serving pool (10000 x 2^22), the
+clustered run-length pools (256 x 2^26) and the co-sparse pool with lists of
+zeros (1500 x 2^24).  The
 oracle checks sampled output word ranges of sampled queries (it computes any
 word range on its own); every cardinality is checked against the popcount of
 the whole returned bitmap."""
@@ -111,3 +113,59 @@ def test_serving_pool_full_size(bm, oracle_lib, dg):
                 srv.release(t)
                 _check_sampled(oracle_lib, dg, words, q, r_bits, got, card,
                                dg.STREAM_TESTS + 18301 + k)
+
+
+def test_rle_clustered_full_size(bm, oracle_lib, dg):
+    """The run-length path on the bench's clustered pool (256 x 2^26, runs of
+    mean 4096 and 8 rows): every word equals the dense path's, sampled ranges
+    equal the oracle's."""
+    r_bits, n = 1 << 26, 256
+    ids = np.arange(n, dtype=np.uint32)
+    queries = [dg.Query(ids, 0, theta=2), dg.Query(ids, 0, theta=128), dg.Query(ids, 1, lo=2, hi=10)]
+    for mean_run in (4096.0, 8.0):
+        words = dg.runs(dg.STREAM_CONFIG2, r_bits, dg.config2_density(n), mean_run)
+        with bm.Pool(r_bits, n) as pool:
+            pool.put_dense(words)
+            pool.put_rle()
+            out_d, out_r = pool.empty_words(), pool.empty_words()
+            cd = torch.zeros(1, dtype=torch.int64, device="cuda")
+            cr = torch.zeros(1, dtype=torch.int64, device="cuda")
+            for k, q in enumerate(queries):
+                bm.query_run(pool, q, out_d, cd, path=bm.PATH_DENSE)
+                bm.query_run(pool, q, out_r, cr, path=bm.PATH_RLE)
+                torch.cuda.synchronize()
+                pool.status()
+                assert torch.equal(out_d, out_r), (mean_run, k)
+                assert int(cd.item()) == int(cr.item())
+                _check_sampled(oracle_lib, dg, words, q, r_bits, bm.to_numpy_words(out_r),
+                               int(cr.item()), dg.STREAM_TESTS + 18600 + k)
+
+
+def test_lists_of_zeros_full_size(bm, oracle_lib, dg):
+    """Co-sparse pool of the bench (1500 x 2^24, half the bitmaps given by
+    their zeros): ScanCount equals the dense path on every word."""
+    r_bits, nbm = 1 << 24, 1500
+    half = nbm // 2
+    d = dg.pool_densities(dg.STREAM_SPARSE + (11 << 32), nbm, 1e-5, 1e-2)
+    d[half:] = 1.0 - d[half:]
+    words = dg.bernoulli(dg.STREAM_SPARSE + (12 << 32), r_bits, d)
+    flat1, offs1 = dg.positions(words[:half], r_bits)
+    flat0, offs0 = dg.positions(~words[half:], r_bits)
+    with bm.Pool(r_bits, nbm) as pool:
+        pool.put_dense(words)
+        pool.put_positions(flat1, offs1)
+        pool.put_positions(flat0, offs0, first_id=half, zeros=True)
+        out_d, out_s = pool.empty_words(), pool.empty_words()
+        cd = torch.zeros(1, dtype=torch.int64, device="cuda")
+        cs = torch.zeros(1, dtype=torch.int64, device="cuda")
+        for n in (1500, 300, 16):
+            ids = dg.floyd(dg.STREAM_SPARSE + (13 << 32) + n, nbm, n)
+            q = dg.Query(ids, 0, theta=n // 2 + 1)
+            bm.query_run(pool, q, out_d, cd, path=bm.PATH_DENSE)
+            bm.query_run(pool, q, out_s, cs, path=bm.PATH_SPARSE)
+            torch.cuda.synchronize()
+            pool.status()
+            assert torch.equal(out_d, out_s), n
+            assert int(cd.item()) == int(cs.item())
+            _check_sampled(oracle_lib, dg, words, q, r_bits, bm.to_numpy_words(out_s),
+                           int(cs.item()), dg.STREAM_TESTS + 18700 + n)
