@@ -211,7 +211,8 @@ int bm_pool_get_sparse_config(bm_pool* pool, bm_sparse_config_t* cfg);
 
 /*
  * Shape of the batch kernel: dense persistent CTAs per SM (1 or 2), adder
- * layout (0, 1 or 2) and words per thread (as for the dense kernel).
+ * layout (0, 1 or 2) and words per thread (as for the dense kernel; here the
+ * 32-input blocks also take one word per thread).
  */
 typedef struct bm_batch_config_t {
     int32_t ctas_per_sm, adder, words_per_thread;

@@ -388,12 +388,12 @@ static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, uint32_t m
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sparse_batch_smem(kSparseMaxWords)));
 #define BM_BATCH_DISPATCH(LL)                                                      \
-    if (adder == 2 && LL == 4) {                                                   \
-        if (K <= 5) return dense_fn(dense_batch_kernel<5, 16, 4>);                 \
-        if (K <= 9) return dense_fn(dense_batch_kernel<9, 32, 4>);                 \
-        if (K <= 11) return dense_fn(dense_batch_kernel<11, 32, 4>);               \
-        if (K <= 13) return dense_fn(dense_batch_kernel<13, 32, 4>);               \
-        return dense_fn(dense_batch_kernel<17, 32, 4>);                            \
+    if (adder == 2) {                                                              \
+        if (K <= 5) return dense_fn(dense_batch_kernel<5, 16, LL>);                \
+        if (K <= 9) return dense_fn(dense_batch_kernel<9, 32, LL>);                \
+        if (K <= 11) return dense_fn(dense_batch_kernel<11, 32, LL>);              \
+        if (K <= 13) return dense_fn(dense_batch_kernel<13, 32, LL>);              \
+        return dense_fn(dense_batch_kernel<17, 32, LL>);                           \
     }                                                                              \
     if (adder == 1) {                                                              \
         if (K <= 5) return dense_fn(dense_batch_kernel<5, 8, LL>);                 \
@@ -619,8 +619,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
 
 extern "C" int bm_pool_set_batch_config(bm_pool* p, const bm_batch_config_t* c) {
     if (!p || !c || c->ctas_per_sm < 1 || c->ctas_per_sm > 2 || c->adder < 0 || c->adder > 2 ||
-        (c->words_per_thread != 1 && c->words_per_thread != 2) ||
-        (c->adder == 2 && c->words_per_thread != 2))
+        (c->words_per_thread != 1 && c->words_per_thread != 2))
         return BM_EINVAL;
     std::lock_guard<std::mutex> lk(p->mu);
     BatchState* b = state(p);

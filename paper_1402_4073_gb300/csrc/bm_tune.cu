@@ -22,7 +22,7 @@ struct Tuned {
 
 // Bumped whenever kernel shapes or their parameters change meaning, so that
 // entries tuned for other kernels are not reused.
-constexpr int kTuneVersion = 2;
+constexpr int kTuneVersion = 3;
 
 std::string cache_key(const bm_pool* p, bool lists) {
     cudaDeviceProp prop{};
