@@ -210,7 +210,8 @@ int bm_pool_set_sparse_config(bm_pool* pool, const bm_sparse_config_t* cfg);
 int bm_pool_get_sparse_config(bm_pool* pool, bm_sparse_config_t* cfg);
 
 /*
- * Shape of the batch kernel: dense persistent CTAs per SM (1 or 2), adder
+ * Shape of the batch kernel: dense persistent CTAs per SM (1 to 3; 3 only
+ * resides with words_per_thread 1), adder
  * layout (0, 1 or 2) and words per thread (as for the dense kernel; here the
  * 32-input blocks also take one word per thread).
  */

@@ -86,8 +86,9 @@ __device__ __forceinline__ void block_card_add(unsigned long long card, unsigned
     }
 }
 
+// One-word columns (L = 2) hold half the planes: three CTAs fit per SM.
 template <int K, int G, int L>
-__global__ void __launch_bounds__(kBatchThreads, 2)
+__global__ void __launch_bounds__(kBatchThreads, L == 2 ? 3 : 2)
     dense_batch_kernel(BatchHeader* h, BatchPoolArgs pa) {
     __shared__ unsigned long long item_s;
     __shared__ unsigned long long part[kBatchThreads / 32];
@@ -618,7 +619,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
 }
 
 extern "C" int bm_pool_set_batch_config(bm_pool* p, const bm_batch_config_t* c) {
-    if (!p || !c || c->ctas_per_sm < 1 || c->ctas_per_sm > 2 || c->adder < 0 || c->adder > 2 ||
+    if (!p || !c || c->ctas_per_sm < 1 || c->ctas_per_sm > 3 || c->adder < 0 || c->adder > 2 ||
         (c->words_per_thread != 1 && c->words_per_thread != 2))
         return BM_EINVAL;
     std::lock_guard<std::mutex> lk(p->mu);

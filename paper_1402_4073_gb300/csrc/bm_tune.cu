@@ -207,9 +207,10 @@ extern "C" int bm_pool_autotune(bm_pool* p, const char* cache_path, char* report
                 bq[i].path = BM_PATH_DENSE;
             }
             best = 1e30;
-            for (int ct : {1, 2})
+            for (int ct : {1, 2, 3})
                 for (int ad : {0, 1, 2})
                     for (int w : {2, 1}) {
+                        if (ct == 3 && w != 1) continue;  // three CTAs per SM only fit one-word columns
                         bm_batch_config_t c{ct, ad, w};
                         if (bm_pool_set_batch_config(p, &c)) continue;
                         rc = time_us(s, [&] {

@@ -44,7 +44,7 @@ def _batch(bm, pool, queries, paths=None):
 
 
 @pytest.mark.parametrize("batch_cfg", [(2, 0, 2), (1, 0, 2), (2, 1, 2), (2, 0, 1), (1, 1, 1),
-                                       (2, 2, 2), (2, 2, 1)])
+                                       (2, 2, 2), (2, 2, 1), (3, 0, 1)])
 def test_batch_matches_oracle(bm, oracle_lib, dg, mixed, batch_cfg):
     r_bits, words, flat, offs, queries = mixed
     with bm.Pool(r_bits, words.shape[0]) as pool:
