@@ -53,6 +53,12 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def alu_peak_ops() -> float:
+    """Integer lane-ops per second of one GB300: SMs x 64 int32 lanes per SM
+    per clock x the maximum SM clock (2070 MHz)."""
+    return 152 * 64 * 2.07e9
+
+
 def sources_sha() -> str:
     h = hashlib.sha256()
     for s in DENSE_SOURCES:
@@ -204,8 +210,18 @@ def bench_batched(bm, datagen, passes: int = 2, small: bool = False):
     same = bool(torch.equal(cards_plain, cards_batch))
     pool.status()
     logical = sum(query_bytes(q.n, r_bits) for q in queries)
+    # integer roofline: ~2 three-input logic ops per 32-bit input word (one
+    # full adder per input in the sideways-sum tree, Sec. 4.3), against
+    # SMs x 64 int32 lanes x the maximum SM clock
+    ops = sum(2 * q.n * ((r_bits + 31) // 32) for q in queries)
+    peak_ops = alu_peak_ops()
     pool.close()
-    return {"workload": f"mixed: {nbm} x 2^{r_bits.bit_length() - 1} pool (densities log-uniform "
+    return {"alu_roofline": {"bound": "alu", "achieved_Tops": round(ops / t_batch / 1e12, 2),
+                             "peak_Tops": round(peak_ops / 1e12, 2),
+                             "frac": round(ops / t_batch / peak_ops, 4),
+                             "ops": "2 LOP3 per 32-bit input word",
+                             "peak_source": "152 SMs x 64 int32 lanes x 2070 MHz (recipe unit counts)"},
+            "workload": f"mixed: {nbm} x 2^{r_bits.bit_length() - 1} pool (densities log-uniform "
                         f"[1e-4,0.5]), {nq} queries N log-uniform [3,{min(1000, nbm)}], 10% intervals",
             "plain_queries_per_s": round(len(queries) / t_plain, 1),
             "batched_queries_per_s": round(len(queries) / t_batch, 1),
