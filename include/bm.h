@@ -196,8 +196,10 @@ int bm_pool_set_dense_config(bm_pool* pool, const bm_dense_config_t* cfg);
 int bm_pool_get_dense_config(bm_pool* pool, bm_dense_config_t* cfg);
 
 /*
- * Shape of the sparse (ScanCount) kernel: tile_rows rows of counters per CTA
- * (a multiple of 8192, at most 65536), `threads` per CTA (64..512, a
+ * Shape of the sparse (ScanCount) kernel: tile_rows rows of 16-bit counters
+ * per CTA (a multiple of 8192, at most 65536; a query of at most 255 inputs
+ * counts in 8 bits over twice the rows, at most 65536, in the same shared
+ * memory), `threads` per CTA (64..512, a
  * multiple of 32), ctas_per_sm (1..8), unroll = 32-vector pieces in each
  * of the two load batches a warp keeps in flight (2 or 4).  BM_EINVAL
  * outside these ranges.

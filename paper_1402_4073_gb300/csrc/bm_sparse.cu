@@ -101,19 +101,24 @@ int launch_sparse(const SparseArgs& a, const SparseConfig& cfg, int sm_count, cu
     // padded lists keep their padding out of every tile of at most 65536 rows
     if (a.tile_rows == 0 || a.tile_rows % kListTileRows || a.tile_rows > 65536) return BM_EINVAL;
     const int bits = a.n <= 255 ? 8 : 16;
+    // tile_rows is sized for 16-bit counters: 8-bit counters take twice the
+    // rows in the same shared memory (at most 65536, where the list padding
+    // stays outside every tile), halving the tiles of a small query
+    SparseArgs b = a;
+    if (bits == 8) b.tile_rows = std::min<uint32_t>(65536u, 2 * a.tile_rows);
     const size_t tab_words = ((size_t)(a.n + 1 + 31) / 32 + 3) & ~(size_t)3;
     const int threads = std::max(64, std::min(512, cfg.threads)) & ~31;
     const size_t scratch_words = (size_t)dev::kScanWarpWords * (size_t)(threads / 32);
     // counters, then one spare word per lane
-    const size_t smem = (tab_words + scratch_words + (size_t)a.tile_rows * bits / 32 + 32) * 4;
-    const uint64_t ntiles = (a.r_bits + a.tile_rows - 1) / a.tile_rows;
+    const size_t smem = (tab_words + scratch_words + (size_t)b.tile_rows * bits / 32 + 32) * 4;
+    const uint64_t ntiles = (b.r_bits + b.tile_rows - 1) / b.tile_rows;
     const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(ntiles, cap));
     auto go = [&](auto fn) -> int {
         if (smem > 48 * 1024)
             BM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem));
-        fn<<<grid, threads, smem, s>>>(a);
+        fn<<<grid, threads, smem, s>>>(b);
         BM_CUDA_TRY(cudaGetLastError());
         return BM_OK;
     };
