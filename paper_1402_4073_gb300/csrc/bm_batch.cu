@@ -87,21 +87,25 @@ __device__ __forceinline__ void block_card_add(unsigned long long card, unsigned
 }
 
 // One-word columns (L = 2) hold half the planes: three CTAs fit per SM.
+// Thread 0 fetches the next item while the current one is counted, and each
+// warp adds its own share of the cardinality: one barrier per item.
 template <int K, int G, int L>
 __global__ void __launch_bounds__(kBatchThreads, L == 2 ? 3 : 2)
     dense_batch_kernel(BatchHeader* h, BatchPoolArgs pa) {
-    __shared__ unsigned long long item_s;
-    __shared__ unsigned long long part[kBatchThreads / 32];
+    __shared__ unsigned long long item_s[2];
     constexpr uint64_t W = L / 2;  // 64-bit words per thread per input
     const uint64_t ncols = (pa.words + W - 1) / W;
     const uint32_t nd = h->n_dense;
     const uint64_t total = h->dense_items;
-    for (;;) {
-        if (threadIdx.x == 0) item_s = atomicAdd(&h->dense_next, 1ull);
-        __syncthreads();
-        const uint64_t item = item_s;
-        __syncthreads();
+    if (threadIdx.x == 0) item_s[0] = atomicAdd(&h->dense_next, 1ull);
+    __syncthreads();
+    for (uint32_t it = 0;; ++it) {
+        // item_s[it & 1] was published by the barrier that ended the last
+        // iteration; it is overwritten only after the next barrier
+        const uint64_t item = item_s[it & 1];
         if (item >= total) break;
+        unsigned long long next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(&h->dense_next, 1ull);
         const uint64_t tile = item / nd;
         const uint32_t qi = h->dense_list[item % nd];
         const QueryDesc* d = h->desc + qi;
@@ -116,7 +120,12 @@ __global__ void __launch_bounds__(kBatchThreads, L == 2 ? 3 : 2)
             const bool vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
             card = finish_column<K, L>(P, pred, pred.table, pa.r_bits, pa.words, out, col, vec_ok);
         }
-        block_card_add(card, reinterpret_cast<unsigned long long*>(h->out_cards + qi), part);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) card += __shfl_xor_sync(0xFFFFFFFFu, card, o);
+        if ((threadIdx.x & 31) == 0 && card)
+            atomicAdd(reinterpret_cast<unsigned long long*>(h->out_cards + qi), card);
+        if (threadIdx.x == 0) item_s[(it + 1) & 1] = next;
+        __syncthreads();
     }
 }
 
