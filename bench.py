@@ -486,6 +486,51 @@ def bench_rle(bm, datagen, reps: int = 10, small: bool = False):
             "pools": pools}
 
 
+def bench_looped(bm, pool, queries, launch, cards, reps: int = 20):
+    """The main workload's plain thresholds with T or N - T + 1 at most 3
+    (theta = 2 and theta = 255 of N = 256) on the Looped recurrence (Sec. 4.4;
+    theta = 255 through the complement identity) and on the counter planes,
+    median of reps launches each (CUDA events; inputs larger than L2)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    peak, peak_src = peaks()
+
+    def timed(i, q):
+        for _ in range(3):
+            launch(i, q)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        torch.cuda.synchronize()
+        for k in range(reps):
+            ev[2 * k].record(stream)
+            launch(i, q)
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps)) * 1e3
+
+    rows = []
+    for i, q in enumerate(queries):
+        t = min(q.theta, q.n - q.theta + 1) if q.kind == 0 else 0
+        if not 1 <= t <= 3:
+            continue
+        row = {"theta": q.theta, "n": q.n, "t": t}
+        got = {}
+        for max_t, name in ((0, "counter_us"), (3, "looped_us")):
+            pool.set_looped(max_t)
+            row[name] = round(timed(i, q), 1)
+            torch.cuda.synchronize()
+            got[max_t] = int(cards[i].item())
+        row["cards_equal"] = got[0] == got[3]
+        gbps = query_bytes(q.n, R_BITS) / row["looped_us"] / 1e3
+        row["looped_GBps"] = round(gbps, 1)
+        row["looped_frac"] = round(gbps / peak, 4)
+        rows.append(row)
+    pool.set_looped(0)
+    pool.status()
+    return {"workload": WORKLOAD, "kernel": "looped_kernel<t,neg> vs the counter's pick",
+            "peak": f"hbm_gbs of {peak_src}", "timing": f"median of {reps} launches, CUDA events",
+            "queries": rows}
+
+
 def bench_weighted(bm, datagen, reps: int = 5, small: bool = False):
     """Weighted thresholds (Sec. 2.3) on the main benchmark's pool (N = 256 bitmaps of
     r = 2^26 rows): weights uniform in [1, wmax] for wmax = 4, 1000 and 2^20, theta =
@@ -639,8 +684,8 @@ def main():
                     help="rows = 2^r_log2 (smaller cases are for profiling only)")
     ap.add_argument("--dense-config", default="",
                     help="variant,threads,stages,ctas_per_sm[,adder]: skip the variant search")
-    ap.add_argument("--parts", default="dense,sparse,rle,weighted,batch,selector,serving",
-                    help="comma list of dense, sparse, rle, weighted, batch, selector, serving")
+    ap.add_argument("--parts", default="dense,looped,sparse,rle,weighted,batch,selector,serving",
+                    help="comma list of dense, looped, sparse, rle, weighted, batch, selector, serving")
     ap.add_argument("--sparse-config", default="",
                     help="tile_rows,threads,ctas_per_sm,unroll for the sparse part: skip tuning")
     ap.add_argument("--small", action="store_true",
@@ -770,9 +815,11 @@ def main():
                "sample": f"the 4 queries over the first {nw} of {words.shape[1]} words "
                          f"({64 * nw} rows), {dt:.1f} s"}
 
-    pool.close()
     extra = {}
     parts = args.parts.split(",")
+    if "looped" in parts:
+        extra["looped"] = bench_looped(bm, pool, queries, launch, cards)
+    pool.close()
     if "sparse" in parts:
         extra["sparse"] = bench_sparse(bm, datagen, small=args.small, config=args.sparse_config)
     if "rle" in parts:

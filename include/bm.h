@@ -224,6 +224,21 @@ int bm_pool_set_batch_config(bm_pool* pool, const bm_batch_config_t* cfg);
 int bm_pool_get_batch_config(bm_pool* pool, bm_batch_config_t* cfg);
 
 /*
+ * Looped recurrence for small thresholds (Sec. 4.4, Algorithm "Looped"):
+ * with max_t in 1..3, a single dense query whose predicate is a plain
+ * threshold "count >= T" (or its negation "count < T", 1 <= T <= N) with
+ * t = min(T, N - T + 1) <= max_t runs t running ORs per input instead of the
+ * counter planes; the form with N - T + 1 goes through the complement
+ * identity, corrected (Sec. 2.3: NOT theta(T, b) = theta(N - T + 1, NOT b)).
+ * max_t = 0 (the default) turns it off.  Results are identical either way.
+ * Applies to bm_threshold, bm_symmetric and bm_query_run on the dense path;
+ * not to batches, weighted queries or bm_threshold_noalloc.
+ * BM_EINVAL if max_t > 3 or an argument is NULL.
+ */
+int bm_pool_set_looped(bm_pool* pool, uint32_t max_t);
+int bm_pool_get_looped(bm_pool* pool, uint32_t* max_t);
+
+/*
  * Autotuner: time candidate shapes of the dense, sparse (if lists are
  * loaded) and batch kernels on queries over the pool's own bitmaps (CUDA
  * events, median of repeats) and install the fastest of each.  With a

@@ -163,6 +163,11 @@ class Pool:
         c = _native.bm_dense_config_t(variant, threads, stages, ctas_per_sm, adder, words_per_thread)
         check(lib.bm_pool_set_dense_config(self.handle, ctypes.byref(c)), "bm_pool_set_dense_config")
 
+    def set_looped(self, max_t: int) -> None:
+        """Plain thresholds with min(T, N - T + 1) <= max_t (1..3) run the
+        Looped recurrence on the dense path; 0 turns it off."""
+        check(lib.bm_pool_set_looped(self.handle, max_t), "bm_pool_set_looped")
+
     def set_sparse_config(self, tile_rows: int = 32768, threads: int = 512,
                           ctas_per_sm: int = 2, unroll: int = 4) -> None:
         c = _native.bm_sparse_config_t(tile_rows, threads, ctas_per_sm, unroll)
@@ -179,8 +184,10 @@ class Pool:
         check(lib.bm_pool_get_dense_config(self.handle, ctypes.byref(d)))
         check(lib.bm_pool_get_sparse_config(self.handle, ctypes.byref(s)))
         check(lib.bm_pool_get_batch_config(self.handle, ctypes.byref(b)))
+        lp = ctypes.c_uint32()
+        check(lib.bm_pool_get_looped(self.handle, ctypes.byref(lp)))
         as_dict = lambda x: {k: getattr(x, k) for k, _ in x._fields_}
-        return {"dense": as_dict(d), "sparse": as_dict(s), "batch": as_dict(b)}
+        return {"dense": as_dict(d), "sparse": as_dict(s), "batch": as_dict(b), "looped": int(lp.value)}
 
     def autotune(self, cache_path: str | None = None) -> str:
         """Measure kernel shapes on this pool and install the fastest."""

@@ -75,6 +75,8 @@ SIGNATURES = {
     "bm_pool_status": (i32, [vp]),
     "bm_pool_set_dense_config": (i32, [vp, ctypes.POINTER(bm_dense_config_t)]),
     "bm_pool_get_dense_config": (i32, [vp, ctypes.POINTER(bm_dense_config_t)]),
+    "bm_pool_set_looped": (i32, [vp, u32]),
+    "bm_pool_get_looped": (i32, [vp, ctypes.POINTER(u32)]),
     "bm_pool_get_sparse_config": (i32, [vp, ctypes.POINTER(bm_sparse_config_t)]),
     "bm_pool_get_batch_config": (i32, [vp, ctypes.POINTER(bm_batch_config_t)]),
     "bm_pool_autotune": (i32, [vp, ctypes.c_char_p, ctypes.c_char_p, u64]),

@@ -138,7 +138,11 @@ int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<ui
         a.out = out_words;
         a.card = reinterpret_cast<unsigned long long*>(out_card);
         a.err = p->d_err;
-        rc = launch_dense(a, p->dense_cfg, p->sm_count, s);
+        LoopedForm lf{};
+        if (looped_form(pred, n, p->looped_max, &lf))
+            rc = launch_looped(a, lf, p->sm_count, s);
+        else
+            rc = launch_dense(a, p->dense_cfg, p->sm_count, s);
     }
     int rc2 = stage_release(sl, s);
     return rc ? rc : rc2;

@@ -85,6 +85,18 @@ struct DenseConfig {
 
 int launch_dense(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStream_t s);
 
+// The Looped recurrence (Sec. 4.4) for a plain threshold whose T, or whose
+// complement N - T + 1 (Sec. 2.3, corrected), is at most kLoopedMaxT.
+constexpr uint32_t kLoopedMaxT = 3;
+struct LoopedForm {
+    uint32_t t;     // accumulators: min(T, N - T + 1)
+    bool neg;       // through the complement identity (negated inputs and result)
+    uint32_t flip;  // ~0u: the predicate is "count < T"
+};
+// True (and *form set) if pred over n inputs is such a threshold with t <= max_t.
+bool looped_form(const Pred& pred, uint32_t n, uint32_t max_t, LoopedForm* form);
+int launch_looped(const DenseArgs& a, const LoopedForm& f, int sm_count, cudaStream_t s);
+
 // Arguments of one sparse (ScanCount) query launch.
 struct SparseArgs {
     const uint32_t* positions;   // pool list arena
@@ -200,6 +212,7 @@ struct bm_pool {
     int next_slot = 0;
     bm::DenseConfig dense_cfg{0, 256, 4, 2};
     bm::SparseConfig sparse_cfg{32768, 512, 2};
+    uint32_t looped_max = 0;  // plain thresholds with min(T, N-T+1) <= this run Looped
     // learned selector (empty: fixed density rule)
     std::vector<float> sel_params;
     float sel_mean[8] = {}, sel_std[8] = {};
