@@ -163,10 +163,12 @@ def cpu_sample_time(words, queries, r_bits, budget_s: float):
     return nbytes / dt, nw, dt
 
 
-def bench_batched(bm, datagen, passes: int = 2, small: bool = False):
+def bench_batched(bm, datagen, passes: int = 2, small: bool = False, config: str = ""):
     """Mixed batch (2000 x 2^24 pool, 4096 queries): plain one query per
     launch vs one batched graph replay; queries/s of each.  small: 400 x 2^22
-    pool and 512 queries (for profiling only)."""
+    pool and 512 queries (for profiling only).  config: "ctas,adder,words"
+    for the batch kernel instead of the autotuner (the only batch launches are
+    then the warm-up replay and the timed ones)."""
     import torch
     r_bits, nbm, nq = (1 << 22, 400, 512) if small else (1 << 24, 2000, 4096)
     words, _ = datagen.mixed_pool(nbm, r_bits)
@@ -174,7 +176,11 @@ def bench_batched(bm, datagen, passes: int = 2, small: bool = False):
     pool = bm.Pool(r_bits, nbm)
     pool.put_dense(words)
     del words
-    tune = pool.autotune()
+    if config:
+        pool.set_batch_config(*[int(x) for x in config.split(",")])
+        tune = f"batch fixed by --batch-config {config}"
+    else:
+        tune = pool.autotune()
     outs = [pool.empty_words() for _ in queries]
     cards_plain = torch.zeros(len(queries), dtype=torch.int64, device="cuda")
     cards_batch = torch.zeros(len(queries), dtype=torch.int64, device="cuda")
@@ -688,6 +694,8 @@ def main():
                     help="comma list of dense, looped, sparse, rle, weighted, batch, selector, serving")
     ap.add_argument("--sparse-config", default="",
                     help="tile_rows,threads,ctas_per_sm,unroll for the sparse part: skip tuning")
+    ap.add_argument("--batch-config", default="",
+                    help="ctas_per_sm,adder,words_per_thread for the batch part: skip tuning")
     ap.add_argument("--small", action="store_true",
                     help="scaled-down batch/selector/serving workloads (profiling only)")
     args = ap.parse_args()
@@ -827,7 +835,7 @@ def main():
     if "weighted" in parts:
         extra["weighted"] = bench_weighted(bm, datagen, small=args.small)
     if "batch" in parts:
-        extra["batched"] = bench_batched(bm, datagen, small=args.small)
+        extra["batched"] = bench_batched(bm, datagen, small=args.small, config=args.batch_config)
     if "selector" in parts:
         extra["selector"] = bench_selector(bm, datagen, small=args.small)
     if "serving" in parts:

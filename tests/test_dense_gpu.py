@@ -270,6 +270,18 @@ def test_config2_full_size(bm, config2, config2_answers, variant):
             check_equal(got, want, f"kind={q.kind} theta={q.theta}")
 
 
+def test_config2_full_size_looped(bm, config2, config2_answers):
+    """The same queries with the Looped recurrence on (theta = 2 directly,
+    theta = 255 through the complement identity; the others stay on the
+    counter), against the oracle over every word."""
+    words, queries = config2
+    with make_pool(bm, words, 1 << 26) as pool:
+        pool.set_looped(3)
+        for q, want in zip(queries, config2_answers):
+            got = run_query(bm, pool, q)
+            check_equal(got, want, f"looped kind={q.kind} theta={q.theta}")
+
+
 def test_config2_planted_rows(bm, oracle_lib, dg, config2):
     """theta = 128 and 255 select nothing on the pure workload; plant rows
     with 100..256 ones so that both thresholds have answers."""
@@ -287,7 +299,9 @@ def test_config2_planted_rows(bm, oracle_lib, dg, config2):
         pool.set_dense_config(1, 128, 4, 1)
         for theta in (128, 255, 256):
             q = dg.Query(ids, 0, theta=theta)
-            got = run_query(bm, pool, q)
             want = oracle_lib.query(words, q, r_bits)
             assert want[1] > 0 or theta == 256
-            check_equal(got, want, f"planted theta={theta}")
+            for looped in (0, 3):  # 255 and 256 take the Looped form when on
+                pool.set_looped(looped)
+                got = run_query(bm, pool, q)
+                check_equal(got, want, f"planted theta={theta} looped={looped}")
