@@ -87,28 +87,29 @@ __device__ __forceinline__ void block_card_add(unsigned long long card, unsigned
 }
 
 // One-word columns (L = 2) hold half the planes: three CTAs fit per SM.
-// Each warp takes its own items, (32-column slab, query) pairs in slab-major
-// order, with no barrier between the warps of a CTA: lane 0 fetches the next
-// item while the current one is counted, and the warp adds its share of the
-// cardinality.
+// Thread 0 fetches the next item while the current one is counted, and each
+// warp adds its own share of the cardinality: one barrier per item.
 template <int K, int G, int L>
 __global__ void __launch_bounds__(kBatchThreads, L == 2 ? 3 : 2)
     dense_batch_kernel(BatchHeader* h, BatchPoolArgs pa) {
+    __shared__ unsigned long long item_s[2];
     constexpr uint64_t W = L / 2;  // 64-bit words per thread per input
     const uint64_t ncols = (pa.words + W - 1) / W;
     const uint32_t nd = h->n_dense;
     const uint64_t total = h->dense_items;
-    const uint32_t lane = threadIdx.x & 31u;
-    unsigned long long item = 0;
-    if (lane == 0) item = atomicAdd(&h->dense_next, 1ull);
-    item = __shfl_sync(0xFFFFFFFFu, item, 0);
-    while (item < total) {
+    if (threadIdx.x == 0) item_s[0] = atomicAdd(&h->dense_next, 1ull);
+    __syncthreads();
+    for (uint32_t it = 0;; ++it) {
+        // item_s[it & 1] was published by the barrier that ended the last
+        // iteration; it is overwritten only after the next barrier
+        const uint64_t item = item_s[it & 1];
+        if (item >= total) break;
         unsigned long long next = 0;
-        if (lane == 0) next = atomicAdd(&h->dense_next, 1ull);
+        if (threadIdx.x == 0) next = atomicAdd(&h->dense_next, 1ull);
         const uint64_t tile = item / nd;
-        const uint32_t qi = h->dense_list[item - tile * nd];
+        const uint32_t qi = h->dense_list[item % nd];
         const QueryDesc* d = h->desc + qi;
-        const uint64_t col = tile * 32 + lane;
+        const uint64_t col = tile * kBatchThreads + threadIdx.x;
         unsigned long long card = 0;
         if (col < ncols) {
             const Pred pred = d->pred;
@@ -121,8 +122,10 @@ __global__ void __launch_bounds__(kBatchThreads, L == 2 ? 3 : 2)
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) card += __shfl_xor_sync(0xFFFFFFFFu, card, o);
-        if (lane == 0 && card) atomicAdd(reinterpret_cast<unsigned long long*>(h->out_cards + qi), card);
-        item = __shfl_sync(0xFFFFFFFFu, next, 0);
+        if ((threadIdx.x & 31) == 0 && card)
+            atomicAdd(reinterpret_cast<unsigned long long*>(h->out_cards + qi), card);
+        if (threadIdx.x == 0) item_s[(it + 1) & 1] = next;
+        __syncthreads();
     }
 }
 
@@ -572,7 +575,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
     hh->n_sparse = (uint32_t)sparse_list.size();
     const uint64_t wpt = b->cfg.words_per_thread == 1 ? 1 : 2;
     const uint64_t ncols = (p->words + wpt - 1) / wpt;
-    const uint64_t dense_tiles = (ncols + 31) / 32;  // one warp's columns per item
+    const uint64_t dense_tiles = (ncols + kBatchThreads - 1) / kBatchThreads;
     hh->dense_items = dense_tiles * dense_list.size();
     QueryDesc* hd = reinterpret_cast<QueryDesc*>(hb + o_desc);
     uint32_t* hids = reinterpret_cast<uint32_t*>(hb + o_ids);
