@@ -786,28 +786,53 @@ def main():
     achieved = query_bytes(N, R_BITS) / avg_launch_s / 1e9
     peak, peak_src = peaks()
 
-    # end to end through the public API: host ids in, output bitmap and
-    # cardinality copied back to pinned host memory every step.  The copies
-    # run on a second stream, each after its query's kernel (an event), so a
-    # query's result travels while the next query computes.
-    host_out = [torch.empty(pool.words, dtype=torch.int64, pin_memory=True) for _ in queries]
-    host_card = torch.empty(nq, dtype=torch.int64, pin_memory=True)
+    # end to end through the public API: host ids (and tables) in, every
+    # output bitmap and cardinality copied back to pinned host memory every
+    # step.  Each copy runs on a second stream after its query's kernel (an
+    # event), so a query's result travels while the next query computes.
+    # Outputs are double-buffered on both sides: step s + 1 is queued before
+    # the host waits for the copies of step s, and step s + 2, which reuses
+    # step s's device buffers, waits on the device for those copies.
+    nbuf = 2
+    e_outs = [[pool.empty_words() for _ in queries] for _ in range(nbuf)]
+    e_cards = [torch.zeros(nq, dtype=torch.int64, device="cuda") for _ in range(nbuf)]
+    host_out = [[torch.empty(pool.words, dtype=torch.int64, pin_memory=True) for _ in queries]
+                for _ in range(nbuf)]
+    host_card = [torch.empty(nq, dtype=torch.int64, pin_memory=True) for _ in range(nbuf)]
+    copied = [None] * nbuf
     copy_stream = torch.cuda.Stream()
+
+    def e2e_launch(i, q, o, c):
+        if q.kind == 0:
+            bm.threshold(pool, q.ids, q.theta, o, c)
+        else:
+            bm.symmetric(pool, q.ids, tables[i], o, c)
+
     e2e_steps = max(3, min(args.steps, 50))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for s in range(e2e_steps):
+        b = s % nbuf
+        if copied[b] is not None:
+            stream.wait_event(copied[b])  # step s - nbuf's results have left these buffers
         for i, q in enumerate(queries):
-            launch(i, q)
+            e2e_launch(i, q, e_outs[b][i], e_cards[b][i:i + 1])
             done = torch.cuda.Event()
             done.record(stream)
             copy_stream.wait_event(done)
             with torch.cuda.stream(copy_stream):
-                host_out[i].copy_(outs[i], non_blocking=True)
+                host_out[b][i].copy_(e_outs[b][i], non_blocking=True)
         with torch.cuda.stream(copy_stream):
-            host_card.copy_(cards, non_blocking=True)
-        torch.cuda.synchronize()
+            host_card[b].copy_(e_cards[b], non_blocking=True)
+        copied[b] = torch.cuda.Event()
+        copied[b].record(copy_stream)
+        if s >= 1:
+            copied[(s - 1) % nbuf].synchronize()  # the host holds step s - 1's results
+    torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    last = (e2e_steps - 1) % nbuf
+    assert torch.equal(host_card[last], cards.cpu()), "end-to-end cardinalities differ"
+    assert torch.equal(host_out[last][0], outs[0].cpu()), "end-to-end output differs"
     h2d = sum(4 * q.n + (8 * len(tables[i]) if i in tables else 0) for i, q in enumerate(queries))
     d2h = nq * pool.words * 8 + nq * 8
     e2e = step_bytes * world / e2e_s / 1e9
