@@ -550,6 +550,7 @@ def bench_weighted(bm, datagen, reps: int = 5, small: bool = False):
     pool.put_dense(words)
     del words
     pool.set_dense_config(0, 256, 4, 2, 2, 2)
+    peak, _ = peaks()
     ids = np.arange(n, dtype=np.uint32)
     out = pool.empty_words()
     card = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -580,7 +581,19 @@ def bench_weighted(bm, datagen, reps: int = 5, small: bool = False):
         if total <= bm.BM_N_MAX:
             rep = np.repeat(ids, w)
             row["replicated_ids_us"] = round(timed(lambda: bm.threshold(pool, rep, theta, out, card)), 1)
-        row["input_GBps"] = round(query_bytes(n, r_bits) / row["weighted_us"] / 1e3, 1)
+        gbps = query_bytes(n, r_bits) / row["weighted_us"] / 1e3
+        row["input_GBps"] = round(gbps, 1)
+        row["hbm_frac"] = round(gbps / peak, 4)
+        # integer work: small weights run as copies (2 logic ops per input word
+        # through the sideways-sum blocks); otherwise weight-1 inputs cost 2 and
+        # each other input 3 per plane of the sum (carry-save full adders)
+        lanes = (r_bits + 31) // 32
+        if total <= bm.BM_N_MAX and total <= 8 * n:
+            ops = 2 * total * lanes
+        else:
+            n1 = int((w == 1).sum())
+            ops = (2 * n1 + 3 * total.bit_length() * int((w > 1).sum())) * lanes
+        row["alu_frac"] = round(ops / (row["weighted_us"] * 1e-6) / alu_peak_ops(), 4)
         rows.append(row)
     pool.status()
     pool.close()

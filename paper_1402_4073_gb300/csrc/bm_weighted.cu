@@ -5,14 +5,17 @@
 // the result may then be ANDed, ORed or AND-NOTed with one more bitmap of the
 // pool in the same pass (the result of a threshold is again a bitmap, Sec. 1).
 //
-// GPU form: a thread owns a column of one or two 64-bit words and keeps K
-// counter planes (the bits of the weighted sum of its rows) in registers.  Inputs of
-// weight 1 go through the sixteen-input sideways-sum blocks of the dense
-// kernel.  An input of weight w > 1 is added once per set bit j of w, at plane
-// j, by rippling its word upwards (half adders); the warp stops a ripple as
-// soon as no lane carries.  When the weights are small (their sum at most 8
-// per input and within BM_N_MAX) they are expanded into copies instead, which
-// the sideways-sum blocks add faster than ripples.  The predicate is the
+// GPU form: a thread owns a column of one or two 64-bit words and keeps the
+// weighted sum of its rows in registers in carry-save form: K sum planes P
+// and K carry planes C, the sum being P + C.  Inputs of weight 1 go through
+// the sixteen-input sideways-sum blocks of the dense kernel into P.  An input
+// x of weight w > 1 is the K-bit number whose plane j is x where bit j of w
+// is set; it joins P and C through one full adder per plane (sum to P_j, carry
+// to C_{j+1}), so its cost is 3 logic operations per plane, with no carry
+// ripple and every plane independent of the others.  One ripple-carry
+// addition of C into P ends the column.  When the weights are small (their
+// sum at most 8 per input and within BM_N_MAX) they are expanded into copies
+// instead, which the sideways-sum blocks add faster.  The predicate is the
 // runtime comparator of the dense kernel against theta - 1.
 #include <algorithm>
 #include <vector>
@@ -40,18 +43,33 @@ struct WeightedArgs {
     unsigned long long* card;
 };
 
-// Add word c at plane j (weight 2^j) and ripple the carries upwards; the warp
-// leaves as soon as no lane carries.  j is the same in every lane.
+// Add the number whose plane j is x where bit j of w is set to the
+// carry-save pair (P, C): a full adder per plane, planes taken from the top
+// so that C_{j+1} is read before the carry of plane j replaces it.  The sum
+// of the pair stays below 2^K (K holds the largest weighted sum), so no carry
+// leaves plane K - 1.
 template <int K>
-__device__ __forceinline__ void add_at(uint32_t (&P)[K], uint32_t c, uint32_t j) {
+__device__ __forceinline__ void csa_weighted(uint32_t (&P)[K], uint32_t (&C)[K], uint32_t x,
+                                             uint32_t w) {
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
-        if ((uint32_t)i >= j) {
-            const uint32_t t = P[i] & c;
-            P[i] ^= c;
-            c = t;
-            if ((i & 1) && !__any_sync(0xFFFFFFFFu, c != 0u)) break;
-        }
+    for (int j = K - 1; j >= 0; --j) {
+        const uint32_t a = x & (0u - ((w >> j) & 1u));
+        const uint32_t carry = maj3(P[j], C[j], a);
+        P[j] = xor3(P[j], C[j], a);
+        if (j + 1 < K) C[j + 1] = carry;
+    }
+    C[0] = 0u;
+}
+
+// P <- P + C (ripple-carry addition; the sum fits in K planes).
+template <int K>
+__device__ __forceinline__ void resolve_carries(uint32_t (&P)[K], const uint32_t (&C)[K]) {
+    uint32_t cy = 0u;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const uint32_t s = xor3(P[j], C[j], cy);
+        cy = maj3(P[j], C[j], cy);
+        P[j] = s;
     }
 }
 
@@ -60,53 +78,64 @@ template <int K, int L>
 __global__ void __launch_bounds__(256) weighted_kernel(WeightedArgs a) {
     constexpr uint32_t W = L / 2;  // words per thread
     const uint64_t ncols = (a.words + W - 1) / W;
-    for (uint64_t col = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;; col += (uint64_t)gridDim.x * blockDim.x) {
-        // the whole warp stays in the loop while any lane has a column (ripples vote)
-        if (!__any_sync(0xFFFFFFFFu, col < ncols)) break;
-        const bool mine = col < ncols;
-        const uint64_t c = mine ? col : ncols - 1;  // idle lanes reread a valid column
-        const uint64_t w0 = W * c;                  // first word of the column
+    const bool vec_ok = ((reinterpret_cast<uintptr_t>(a.out) & 15u) == 0);
+    unsigned long long card = 0;
+    for (uint64_t col = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; col < ncols;
+         col += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t w0 = W * col;  // first word of the column
         uint32_t P[L][K];
         zero_planes<K, L>(P);
         count_column<K, 16, L>(P, a.base + w0, a.ids1, a.n1, a.stride_words);
-        // weighted inputs, the next one's word in flight while this one ripples
-        Slice<L> x_next;
-        if (a.nw) x_next = ld_slice<L>(a.base + (uint64_t)__ldg(a.idsw) * a.stride_words + w0);
-        for (uint32_t k = 0; k < a.nw; ++k) {
-            const Slice<L> x = x_next;
-            uint32_t w = __ldg(a.wts + k);
-            if (k + 1 < a.nw)
-                x_next = ld_slice<L>(a.base + (uint64_t)__ldg(a.idsw + k + 1) * a.stride_words + w0);
-            while (w) {
-                const uint32_t j = __ffs(w) - 1;
-                w &= w - 1;
+        if (a.nw) {
+            uint32_t C[L][K];
+            zero_planes<K, L>(C);
+            // weighted inputs, the next one's word in flight while this one is added
+            Slice<L> x_next = ld_slice<L>(a.base + (uint64_t)__ldg(a.idsw) * a.stride_words + w0);
+            for (uint32_t k = 0; k < a.nw; ++k) {
+                const Slice<L> x = x_next;
+                const uint32_t w = __ldg(a.wts + k);
+                if (k + 1 < a.nw)
+                    x_next = ld_slice<L>(a.base + (uint64_t)__ldg(a.idsw + k + 1) * a.stride_words + w0);
 #pragma unroll
-                for (int l = 0; l < L; ++l) add_at<K>(P[l], x.v[l], j);
+                for (int l = 0; l < L; ++l) csa_weighted<K>(P[l], C[l], x.v[l], w);
             }
+#pragma unroll
+            for (int l = 0; l < L; ++l) resolve_carries<K>(P[l], C[l]);
         }
-        unsigned long long ones = 0;
+        uint64_t word[W];
+#pragma unroll
+        for (uint32_t i = 0; i < W; ++i)
+            word[i] = a.all ? ~0ull
+                            : ((uint64_t)greater_than<K>(P[2 * i], (uint32_t)(a.theta - 1)) |
+                               ((uint64_t)greater_than<K>(P[2 * i + 1], (uint32_t)(a.theta - 1)) << 32));
 #pragma unroll
         for (uint32_t i = 0; i < W; ++i) {
             const uint64_t wi = w0 + i;
-            uint64_t word = a.all ? ~0ull
-                                  : ((uint64_t)greater_than<K>(P[2 * i], (uint32_t)(a.theta - 1)) |
-                                     ((uint64_t)greater_than<K>(P[2 * i + 1], (uint32_t)(a.theta - 1)) << 32));
             if (wi < a.words) {
                 if (a.post_op) {
                     const uint64_t m = __ldg(a.post + wi);
-                    word = a.post_op == BM_POST_AND ? (word & m)
-                         : a.post_op == BM_POST_OR  ? (word | m)
-                                                    : (word & ~m);
+                    word[i] = a.post_op == BM_POST_AND ? (word[i] & m)
+                            : a.post_op == BM_POST_OR  ? (word[i] | m)
+                                                       : (word[i] & ~m);
                 }
-                if (wi == a.words - 1 && (a.r_bits & 63u)) word &= (1ull << (a.r_bits & 63u)) - 1ull;
-                if (mine) {
-                    a.out[wi] = word;
-                    ones += (unsigned long long)__popcll(word);
-                }
+                if (wi == a.words - 1 && (a.r_bits & 63u)) word[i] &= (1ull << (a.r_bits & 63u)) - 1ull;
+            } else {
+                word[i] = 0;
             }
         }
-        flush_card(ones, a.card);
+        if (W == 2 && w0 + 1 < a.words && vec_ok) {
+            asm volatile("st.global.v2.u64 [%0], {%1, %2};" ::"l"(a.out + w0), "l"(word[0]),
+                         "l"(word[W - 1])
+                         : "memory");
+        } else {
+#pragma unroll
+            for (uint32_t i = 0; i < W; ++i)
+                if (w0 + i < a.words) a.out[w0 + i] = word[i];
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < W; ++i) card += (unsigned long long)__popcll(word[i]);
     }
+    flush_card(card, a.card);
 }
 
 template <int K, int L>
@@ -208,8 +237,12 @@ extern "C" int bm_weighted_threshold(bm_pool* p, const bm_weighted_query* q, uin
             rc = launch_k<12, 4>(a, p->sm_count, s);
         else if (planes <= 16)
             rc = launch_k<16, 2>(a, p->sm_count, s);
+        else if (planes <= 20)  // a weighted input costs 3 operations per plane
+            rc = launch_k<20, 2>(a, p->sm_count, s);
         else if (planes <= 24)
             rc = launch_k<24, 2>(a, p->sm_count, s);
+        else if (planes <= 28)
+            rc = launch_k<28, 2>(a, p->sm_count, s);
         else
             rc = launch_k<32, 2>(a, p->sm_count, s);
     }
