@@ -54,9 +54,10 @@ def test_weighted_small(bm, oracle_lib, dg, r_bits):
             assert np.array_equal(got[0], want[0]) and got[1] == want[1], theta
 
 
-@pytest.mark.parametrize("wmax", [300, 70000, (1 << 24) - 1])
+@pytest.mark.parametrize("wmax", [25, 300, 2000, 70000, 500000, (1 << 24) - 1])
 def test_weighted_large(bm, oracle_lib, dg, wmax):
-    """Sums past 2^8, 2^16 and 2^24 (16, 24 and 32 counter planes)."""
+    """Sums of about 2^12, 2^16, 2^18, 2^23, 2^26 and 2^31: every compiled
+    plane count from 12 to 32 (weights too large to run as copies)."""
     r_bits = 20000
     n = 300
     words = dg.bernoulli(dg.STREAM_TESTS + 21100, r_bits, np.linspace(0.02, 0.9, 50))
@@ -75,6 +76,24 @@ def test_weighted_large(bm, oracle_lib, dg, wmax):
         got = _run(bm, pool, ids, weights, s // 2, 3, 49)
         want = oracle_lib.weighted(words, ids, weights, r_bits, s // 2, 3, words[49])
         assert np.array_equal(got[0], want[0]) and got[1] == want[1]
+
+
+def test_weighted_eight_planes(bm, oracle_lib, dg):
+    """A sum of 8 planes above 8 per input (no copies): the smallest
+    carry-save form, with weight-1 inputs beside it."""
+    r_bits = 64 * 300 + 9
+    words = dg.bernoulli(dg.STREAM_TESTS + 21300, r_bits, np.linspace(0.05, 0.95, 20))
+    ids = np.arange(20, dtype=np.uint32)
+    weights = np.full(20, 12, dtype=np.uint32)
+    weights[:3] = 1
+    s = int(weights.sum())
+    assert 8 * 20 < s < 256
+    with bm.Pool(r_bits, 20) as pool:
+        pool.put_dense(words)
+        for theta in (1, 12, 13, 100, s - 1, s):
+            got = _run(bm, pool, ids, weights, theta)
+            want = oracle_lib.weighted(words, ids, weights, r_bits, theta)
+            assert np.array_equal(got[0], want[0]) and got[1] == want[1], theta
 
 
 def test_weighted_errors(bm, dg):
