@@ -165,7 +165,7 @@ __device__ __forceinline__ uint64_t eval_offset(const uint32_t (&P)[2][K], const
 }
 
 template <int K>
-__global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2) rle_kernel(RleArgs a) {
+__global__ void __launch_bounds__(kRleThreads, K <= 9 ? 4 : (K <= 13 ? 3 : 2)) rle_kernel(RleArgs a) {
     extern __shared__ __align__(16) uint64_t sm64[];
     uint64_t* stage = sm64;                                                    // [kRleGroup][256]
     uint2* dirty = reinterpret_cast<uint2*>(stage + kRleGroup * kRleThreads);  // [kRleChunk]
