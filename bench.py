@@ -480,8 +480,11 @@ def bench_rle(bm, datagen, reps: int = 10, small: bool = False):
                          "rle_achieved_GBps": round(alg / t[bm.PATH_RLE] / 1e3, 1),
                          "rle_frac": round(alg / t[bm.PATH_RLE] / 1e3 / peak, 4)})
         pool.status()
+        # what BM_PATH_AUTO takes for these single queries (run-length or dense)
+        auto = {bm.PATH_DENSE: "dense", bm.PATH_SPARSE: "sparse", bm.PATH_RLE: "rle"}
         pools.append({"mean_run_rows": mean_run, "runs": runs, "literal_words": lits,
                       "rle_bytes_per_query": alg, "dense_bytes_per_query": query_bytes(n, r_bits),
+                      "auto_path": auto.get(bm.query_select(pool, queries[0])[0], "?"),
                       "queries": rows})
         pool.close()
     return {"workload": f"clustered dense: N={n} bitmaps x r=2^{r_bits.bit_length() - 1} rows, "

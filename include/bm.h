@@ -285,7 +285,10 @@ int bm_symmetric(bm_pool* pool, const uint32_t* ids, uint32_t n, const uint64_t*
 #define BM_PATH_DENSE 1  /* bit-sliced carry-save counter over the dense words */
 #define BM_PATH_SPARSE 2 /* ScanCount over the position lists (every id needs a list) */
 #define BM_PATH_RLE 3    /* run-length form with clean-run pruning (every id needs one);
-                            single queries only, never chosen by BM_PATH_AUTO */
+                            single queries only.  BM_PATH_AUTO takes it for a single
+                            query in place of the dense counter when every id has one
+                            and its runs, literal words and tile summaries are
+                            estimated faster to read than the dense words */
 
 typedef struct bm_query {
     const uint32_t* ids;    /* host array of n pool ids (repeats allowed) */
@@ -506,7 +509,8 @@ int bm_query_features(const bm_pool* pool, const bm_query* q, float* out);
 int bm_pool_set_selector(bm_pool* pool, const float* params, uint64_t nparams, const float* mean,
                          const float* stdev, uint32_t n_out);
 
-/* The path and sparse tile rows that BM_PATH_AUTO would pick for q. */
+/* The path and sparse tile rows that BM_PATH_AUTO would pick for q as a
+   single query (bm_query_run). */
 int bm_query_select(const bm_pool* pool, const bm_query* q, int32_t* path, uint32_t* tile_rows);
 
 /*

@@ -192,7 +192,7 @@ int bm_query_run(bm_pool* p, const bm_query* q, uint64_t* out_card, int32_t* cho
     if (rc) return rc;
     BM_CUDA_TRY(cudaSetDevice(p->device));
     Candidate c{q->path, 0};
-    if (q->path == BM_PATH_AUTO) c = select_candidate(p, q->ids, q->n, f);
+    if (q->path == BM_PATH_AUTO) c = single_query_candidate(p, q->ids, q->n, f);
     if (chosen_path) *chosen_path = c.path;
     return run_single(p, q->ids, q->n, f, c.path, c.tile_rows, q->out_words, out_card,
                       static_cast<cudaStream_t>(stream));

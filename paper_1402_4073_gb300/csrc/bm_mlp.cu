@@ -234,7 +234,7 @@ int bm_query_select(const bm_pool* p, const bm_query* q, int32_t* path, uint32_t
     std::vector<uint8_t> f;
     rc = query_truth(q, f);
     if (rc) return rc;
-    Candidate c = select_candidate(p, q->ids, q->n, f);
+    Candidate c = single_query_candidate(p, q->ids, q->n, f);
     *path = c.path;
     if (tile_rows) *tile_rows = c.tile_rows ? c.tile_rows : p->sparse_cfg.tile_rows;
     return BM_OK;

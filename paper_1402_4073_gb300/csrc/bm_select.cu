@@ -1,4 +1,5 @@
 // Per-query kernel choice: features, fixed rule, learned selector.
+#include <algorithm>
 #include <cmath>
 
 #include "bm_select.h"
@@ -89,6 +90,30 @@ Candidate select_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
         if (best < 0 || y[c] < y[best]) best = c;
     }
     return best < 0 ? kCandidateTable[0] : kCandidateTable[best];
+}
+
+// Cost of a single query on GB300, fitted to the measured kernels (N = 256,
+// r = 2^26): the dense counter streams its bytes at the HBM rate; the
+// run-length kernel pays a latency chain of about 6 us per round of tiles
+// across the GPU (four CTAs per SM, one tile each) plus about 1.6 us per MB
+// of runs, literal words and tile summaries (runs of mean 4096, 256 and 8
+// rows: 51, 130 and 650 us against about 42 + 1.6 x 6.4, 34.6 and 380 MB).
+constexpr double kDenseUsPerMB = 0.145, kDenseFixedUs = 5.0;
+constexpr double kRleUsPerMB = 1.6, kRleRoundUs = 6.0;
+
+Candidate single_query_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
+                                 const std::vector<uint8_t>& f) {
+    const Candidate c = select_candidate(p, ids, n, f);
+    if (c.path != BM_PATH_DENSE || !all_have(p->rle_present, ids, n)) return c;
+    uint64_t words = 0;  // runs and literal words, 8 bytes each
+    for (uint32_t k = 0; k < n; ++k) words += p->rle_runs[ids[k]] + p->rle_lits[ids[k]];
+    const double tiles = (double)((p->words + kRleTileWords - 1) / kRleTileWords);
+    const double rle_mb = (8.0 * (double)words + 4.0 * (double)n * tiles) / 1e6;
+    const double dense_mb = (double)n * (double)p->r_bits / 8.0 / 1e6;
+    const double rounds = std::ceil(tiles / (4.0 * (double)std::max(1, p->sm_count)));
+    if (kRleRoundUs * rounds + kRleUsPerMB * rle_mb < kDenseFixedUs + kDenseUsPerMB * dense_mb)
+        return Candidate{BM_PATH_RLE, 0};
+    return c;
 }
 
 }  // namespace bm

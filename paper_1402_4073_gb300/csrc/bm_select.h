@@ -15,7 +15,7 @@ constexpr int kHidden = 64;
 
 // The kernel configurations a query can run on (the selector's outputs).
 struct Candidate {
-    int path;            // BM_PATH_DENSE or BM_PATH_SPARSE
+    int path;            // BM_PATH_DENSE, BM_PATH_SPARSE (or BM_PATH_RLE: single queries)
     uint32_t tile_rows;  // sparse tile (0 for dense)
 };
 constexpr int kCandidates = 4;
@@ -35,6 +35,13 @@ Candidate rule_choice(const bm_pool* p, const uint32_t* ids, uint32_t n);
 // inputs are missing (no lists, no dense words) are never chosen.
 Candidate select_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
                            const std::vector<uint8_t>& f);
+
+// A single query's choice: select_candidate, then the run-length path in
+// place of the dense counter when every input has a run-length form and the
+// estimated time of reading its runs, literal words and tile summaries is
+// below that of reading the dense words (batches have no run-length items).
+Candidate single_query_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
+                                 const std::vector<uint8_t>& f);
 
 // MLP forward on the host for one feature vector (fp32), all C outputs.
 void mlp_forward_host(const float* params, int C, const float* x, float* y);

@@ -132,6 +132,40 @@ def test_rle_clustered_workload_subset(bm, oracle_lib, dg):
             assert np.array_equal(got[0], want[0]) and got[1] == want[1], q
 
 
+def test_rle_auto_selection(bm, oracle_lib, dg):
+    """BM_PATH_AUTO takes the run-length path for a single query over
+    clustered inputs (few runs) and the dense counter over incompressible
+    ones, with the same answers as the oracle either way; batches never
+    receive run-length items."""
+    r_bits = 1 << 23
+    clustered = dg.runs(dg.STREAM_TESTS + 20400, r_bits, np.linspace(0.01, 0.3, 48), 4096.0)
+    scattered = dg.bernoulli(dg.STREAM_TESTS + 20401, r_bits, np.linspace(0.2, 0.5, 48))
+    words = np.concatenate([clustered, scattered])
+    with _pool(bm, words, r_bits) as pool:
+        for ids, want_path in ((np.arange(48), bm.PATH_RLE), (np.arange(48, 96), bm.PATH_DENSE)):
+            ids = ids.astype(np.uint32)
+            for q in (dg.Query(ids, 0, theta=3), dg.Query(ids, 1, lo=2, hi=9)):
+                assert bm.query_select(pool, q)[0] == want_path
+                out = pool.empty_words()
+                out.fill_(-1)
+                card = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+                assert bm.query_run(pool, q, out, card) == want_path
+                torch.cuda.synchronize()
+                pool.status()
+                want = oracle_lib.query(words, q, r_bits)
+                assert np.array_equal(bm.to_numpy_words(out), want[0]) and int(card.item()) == want[1]
+        # in a batch the same clustered query runs on the dense counter
+        q = dg.Query(np.arange(48, dtype=np.uint32), 0, theta=3)
+        out = pool.empty_words()
+        cards = torch.zeros(1, dtype=torch.int64, device="cuda")
+        paths = bm.threshold_batch(pool, [q], [out], cards, paths=[bm.PATH_AUTO])
+        torch.cuda.synchronize()
+        pool.status()
+        assert list(paths) == [bm.PATH_DENSE]
+        want = oracle_lib.query(words, q, r_bits)
+        assert np.array_equal(bm.to_numpy_words(out), want[0]) and int(cards[0].item()) == want[1]
+
+
 def test_rle_errors(bm, dg):
     r_bits = 5000
     words = dg.bernoulli(dg.STREAM_TESTS + 20300, r_bits, np.array([0.1, 0.2, 0.3]))
