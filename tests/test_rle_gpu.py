@@ -154,6 +154,15 @@ def test_rle_auto_selection(bm, oracle_lib, dg):
                 pool.status()
                 want = oracle_lib.query(words, q, r_bits)
                 assert np.array_equal(bm.to_numpy_words(out), want[0]) and int(card.item()) == want[1]
+        # an input without a run-length form keeps the query on the dense counter
+        words2 = words[:49].copy()
+        with bm.Pool(r_bits, 49) as pool2:
+            pool2.put_dense(words2)
+            pool2.put_rle(0, 40)
+            q = dg.Query(np.arange(48, dtype=np.uint32), 0, theta=3)
+            assert bm.query_select(pool2, q)[0] == bm.PATH_DENSE
+            q = dg.Query(np.arange(40, dtype=np.uint32), 0, theta=3)
+            assert bm.query_select(pool2, q)[0] == bm.PATH_RLE
         # in a batch the same clustered query runs on the dense counter
         q = dg.Query(np.arange(48, dtype=np.uint32), 0, theta=3)
         out = pool.empty_words()
