@@ -315,8 +315,8 @@ int bm_query_run(bm_pool* pool, const bm_query* q, uint64_t* out_card, int32_t* 
 /*
  * Batched queries (not in the paper, which runs one query at a time): run
  * the nq queries q[0..nq) as one replay of a CUDA graph holding two
- * persistent kernels.  Dense queries are cut into (32768-row slab, query)
- * items taken slab-major, so each slab of the pool is read from HBM once
+ * persistent kernels.  Dense queries are cut into (slab, query) items, a
+ * slab being 32768 rows (16384 with one word per thread), taken slab-major, so each slab of the pool is read from HBM once
  * and served from L2 to every query of the batch that reads it; sparse
  * queries into (query, row tile) ScanCount items.  BM_PATH_AUTO queries are
  * routed by the learned selector when one is installed (its network runs on
