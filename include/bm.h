@@ -284,11 +284,11 @@ int bm_symmetric(bm_pool* pool, const uint32_t* ids, uint32_t n, const uint64_t*
 #define BM_PATH_AUTO 0   /* the pool's selector chooses (learned model, else a density rule) */
 #define BM_PATH_DENSE 1  /* bit-sliced carry-save counter over the dense words */
 #define BM_PATH_SPARSE 2 /* ScanCount over the position lists (every id needs a list) */
-#define BM_PATH_RLE 3    /* run-length form with clean-run pruning (every id needs one);
-                            single queries only.  BM_PATH_AUTO takes it for a single
-                            query in place of the dense counter when every id has one
-                            and its runs, literal words and tile summaries are
-                            estimated faster to read than the dense words */
+#define BM_PATH_RLE 3    /* run-length form with clean-run pruning (every id needs one).
+                            BM_PATH_AUTO takes it in place of the dense counter when
+                            every id has one and its runs, literal words and tile
+                            summaries are estimated faster to read than the dense
+                            words */
 
 typedef struct bm_query {
     const uint32_t* ids;    /* host array of n pool ids (repeats allowed) */
@@ -318,15 +318,16 @@ int bm_query_run(bm_pool* pool, const bm_query* q, uint64_t* out_card, int32_t* 
  * persistent kernels.  Dense queries are cut into (slab, query) items, a
  * slab being 32768 rows (16384 with one word per thread), taken slab-major, so each slab of the pool is read from HBM once
  * and served from L2 to every query of the batch that reads it; sparse
- * queries into (query, row tile) ScanCount items.  BM_PATH_AUTO queries are
+ * queries into (query, row tile) ScanCount items; run-length queries run
+ * after the graph, one launch of the run-length kernel each, on the same
+ * stream.  BM_PATH_AUTO queries are
  * routed by the learned selector when one is installed (its network runs on
  * the device for the whole batch), else by the density rule.
  * out_cards: device, nq uint64, receives each query's cardinality.
  * chosen_paths: host, nq entries (may be NULL), receives each query's path.
  * Every result equals that of the same query run alone.  Host arrays are
  * copied before the call returns; up to three batches may be in flight.
- * Errors as bm_query_run, for the first failing query (nothing is launched);
- * BM_EINVAL for a query on BM_PATH_RLE (single queries only).
+ * Errors as bm_query_run, for the first failing query (nothing is launched).
  */
 int bm_threshold_batch(bm_pool* pool, const bm_query* q, uint32_t nq, uint64_t* out_cards,
                        int32_t* chosen_paths, void* stream);

@@ -489,7 +489,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
     uint32_t max_dense_n = 1;
     for (uint32_t i = 0; i < nq; ++i) {
         const bm_query& qi = q[i];
-        if (!qi.out_words || qi.reserved || qi.path < BM_PATH_AUTO || qi.path > BM_PATH_SPARSE)
+        if (!qi.out_words || qi.reserved || qi.path < BM_PATH_AUTO || qi.path > BM_PATH_RLE)
             return BM_EINVAL;
         int rc = validate_ids(p, qi.ids, qi.n, qi.path);
         if (!rc) rc = query_truth(&qi, truth[i]);
@@ -501,7 +501,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
                 feats.emplace_back(kFeatures);
                 query_features(p, qi.ids, qi.n, truth[i], feats.back().data());
             } else {
-                cand[i] = rule_choice(p, qi.ids, qi.n);
+                cand[i] = with_rle(p, qi.ids, qi.n, rule_choice(p, qi.ids, qi.n));
             }
         } else {
             cand[i] = Candidate{qi.path, qi.path == BM_PATH_SPARSE ? p->sparse_cfg.tile_rows : 0u};
@@ -522,11 +522,11 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
             }
             if (c.path == BM_PATH_SPARSE && !lists) c = kCandidateTable[0];
             if (c.path == BM_PATH_DENSE && !dense) c = Candidate{BM_PATH_SPARSE, p->sparse_cfg.tile_rows};
-            cand[i] = c;
+            cand[i] = with_rle(p, q[i].ids, q[i].n, c);
         }
     }
     std::vector<Pred> preds(nq);
-    std::vector<uint32_t> dense_list, sparse_list;
+    std::vector<uint32_t> dense_list, sparse_list, rle_list;
     std::vector<uint64_t> sparse_off(1, 0);
     uint32_t max_words = 0;
     for (uint32_t i = 0; i < nq; ++i) {
@@ -541,6 +541,8 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
             sparse_list.push_back(i);
             sparse_off.push_back(sparse_off.back() +
                                  (p->r_bits + cand[i].tile_rows - 1) / cand[i].tile_rows);
+        } else if (cand[i].path == BM_PATH_RLE) {
+            rle_list.push_back(i);
         } else {
             dense_list.push_back(i);
             max_dense_n = std::max(max_dense_n, q[i].n);
@@ -622,6 +624,28 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
     if (rc) return rc;
     BM_CUDA_TRY(cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, s));
     BM_CUDA_TRY(cudaGraphLaunch(ex, s));
+    // run-length queries: one launch each of the run-length kernel after the
+    // graph, reading their ids and tables from the descriptor block and adding
+    // to the cardinalities the graph zeroed
+    for (uint32_t i : rle_list) {
+        RleArgs a{};
+        a.runs = p->d_runs;
+        a.lits = p->d_lits;
+        a.run_begin = p->d_run_begin;
+        a.lit_begin = p->d_lit_begin;
+        a.run_count = p->d_run_count;
+        a.tile_index = p->d_rle_tiles;
+        a.tiles_plus_one = p->rle_tiles + 1;
+        a.words = p->words;
+        a.r_bits = p->r_bits;
+        a.ids = hd[i].ids;
+        a.n = hd[i].n;
+        a.pred = hd[i].pred;  // a table, if any, in the descriptor block
+        a.out = q[i].out_words;
+        a.card = reinterpret_cast<unsigned long long*>(out_cards + i);
+        rc = launch_rle(a, p->sm_count, s);
+        if (rc) return rc;
+    }
     BM_CUDA_TRY(cudaEventRecord(sl.ev, s));
     sl.used = true;
     return BM_OK;

@@ -101,9 +101,7 @@ Candidate select_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
 constexpr double kDenseUsPerMB = 0.145, kDenseFixedUs = 5.0;
 constexpr double kRleUsPerMB = 1.6, kRleRoundUs = 6.0;
 
-Candidate single_query_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
-                                 const std::vector<uint8_t>& f) {
-    const Candidate c = select_candidate(p, ids, n, f);
+Candidate with_rle(const bm_pool* p, const uint32_t* ids, uint32_t n, Candidate c) {
     if (c.path != BM_PATH_DENSE || !all_have(p->rle_present, ids, n)) return c;
     uint64_t words = 0;  // runs and literal words, 8 bytes each
     for (uint32_t k = 0; k < n; ++k) words += p->rle_runs[ids[k]] + p->rle_lits[ids[k]];
@@ -114,6 +112,11 @@ Candidate single_query_candidate(const bm_pool* p, const uint32_t* ids, uint32_t
     if (kRleRoundUs * rounds + kRleUsPerMB * rle_mb < kDenseFixedUs + kDenseUsPerMB * dense_mb)
         return Candidate{BM_PATH_RLE, 0};
     return c;
+}
+
+Candidate single_query_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
+                                 const std::vector<uint8_t>& f) {
+    return with_rle(p, ids, n, select_candidate(p, ids, n, f));
 }
 
 }  // namespace bm

@@ -15,7 +15,7 @@ constexpr int kHidden = 64;
 
 // The kernel configurations a query can run on (the selector's outputs).
 struct Candidate {
-    int path;            // BM_PATH_DENSE, BM_PATH_SPARSE (or BM_PATH_RLE: single queries)
+    int path;            // BM_PATH_DENSE, BM_PATH_SPARSE or BM_PATH_RLE
     uint32_t tile_rows;  // sparse tile (0 for dense)
 };
 constexpr int kCandidates = 4;
@@ -36,10 +36,12 @@ Candidate rule_choice(const bm_pool* p, const uint32_t* ids, uint32_t n);
 Candidate select_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
                            const std::vector<uint8_t>& f);
 
-// A single query's choice: select_candidate, then the run-length path in
-// place of the dense counter when every input has a run-length form and the
-// estimated time of reading its runs, literal words and tile summaries is
-// below that of reading the dense words (batches have no run-length items).
+// The run-length path in place of a dense choice c when every input has a
+// run-length form and the estimated time of reading its runs, literal words
+// and tile summaries is below that of reading the dense words; else c.
+Candidate with_rle(const bm_pool* p, const uint32_t* ids, uint32_t n, Candidate c);
+
+// A single query's choice: select_candidate, then with_rle.
 Candidate single_query_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
                                  const std::vector<uint8_t>& f);
 

@@ -6,7 +6,7 @@ zeros) and random queries (thresholds including theta = 0 and theta > N,
 intervals including count 0, truth tables; repeated ids).  Each query runs
 on the dense counter in three kernel shapes, the Looped recurrence,
 ScanCount, the run-length form and BM_PATH_AUTO, and all of them once more
-as one batch with automatic and explicit paths."""
+as one batch with automatic and explicit paths (run-length ones included)."""
 from __future__ import annotations
 
 import numpy as np
@@ -99,7 +99,8 @@ def test_cross_path_random(bm, oracle_lib, dg, case):
         for o in outs:
             o.fill_(-1)
         cards = torch.full((len(queries),), -1, dtype=torch.int64, device="cuda")
-        paths = [(bm.PATH_AUTO, bm.PATH_DENSE, bm.PATH_SPARSE)[i % 3] for i in range(len(queries))]
+        paths = [(bm.PATH_AUTO, bm.PATH_DENSE, bm.PATH_SPARSE, bm.PATH_RLE)[i % 4]
+                 for i in range(len(queries))]
         bm.threshold_batch(pool, queries, outs, cards, paths=paths)
         torch.cuda.synchronize()
         pool.status()

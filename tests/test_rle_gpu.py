@@ -133,10 +133,9 @@ def test_rle_clustered_workload_subset(bm, oracle_lib, dg):
 
 
 def test_rle_auto_selection(bm, oracle_lib, dg):
-    """BM_PATH_AUTO takes the run-length path for a single query over
-    clustered inputs (few runs) and the dense counter over incompressible
-    ones, with the same answers as the oracle either way; batches never
-    receive run-length items."""
+    """BM_PATH_AUTO takes the run-length path for a query over clustered
+    inputs (few runs) and the dense counter over incompressible ones, alone
+    and in a batch, with the same answers as the oracle either way."""
     r_bits = 1 << 23
     clustered = dg.runs(dg.STREAM_TESTS + 20400, r_bits, np.linspace(0.01, 0.3, 48), 4096.0)
     scattered = dg.bernoulli(dg.STREAM_TESTS + 20401, r_bits, np.linspace(0.2, 0.5, 48))
@@ -163,16 +162,23 @@ def test_rle_auto_selection(bm, oracle_lib, dg):
             assert bm.query_select(pool2, q)[0] == bm.PATH_DENSE
             q = dg.Query(np.arange(40, dtype=np.uint32), 0, theta=3)
             assert bm.query_select(pool2, q)[0] == bm.PATH_RLE
-        # in a batch the same clustered query runs on the dense counter
-        q = dg.Query(np.arange(48, dtype=np.uint32), 0, theta=3)
-        out = pool.empty_words()
-        cards = torch.zeros(1, dtype=torch.int64, device="cuda")
-        paths = bm.threshold_batch(pool, [q], [out], cards, paths=[bm.PATH_AUTO])
+        # in a batch the same choices, beside a dense and a ScanCount-less query
+        qs = [dg.Query(np.arange(48, dtype=np.uint32), 0, theta=3),
+              dg.Query(np.arange(48, 96, dtype=np.uint32), 0, theta=3),
+              dg.Query(np.arange(0, 96, 2, dtype=np.uint32), 2,
+                       table=dg.table_from_bools(np.arange(49) % 3 == 1))]
+        outs = [pool.empty_words() for _ in qs]
+        for o in outs:
+            o.fill_(-1)
+        cards = torch.full((len(qs),), -1, dtype=torch.int64, device="cuda")
+        paths = bm.threshold_batch(pool, qs, outs, cards, paths=[bm.PATH_AUTO, bm.PATH_AUTO, bm.PATH_RLE])
         torch.cuda.synchronize()
         pool.status()
-        assert list(paths) == [bm.PATH_DENSE]
-        want = oracle_lib.query(words, q, r_bits)
-        assert np.array_equal(bm.to_numpy_words(out), want[0]) and int(cards[0].item()) == want[1]
+        assert list(paths) == [bm.PATH_RLE, bm.PATH_DENSE, bm.PATH_RLE]
+        for i, q in enumerate(qs):
+            want = oracle_lib.query(words, q, r_bits)
+            assert np.array_equal(bm.to_numpy_words(outs[i]), want[0]), i
+            assert int(cards[i].item()) == want[1], i
 
 
 def test_rle_errors(bm, dg):
@@ -189,9 +195,9 @@ def test_rle_errors(bm, dg):
         with pytest.raises(bm.BMError) as e:  # id 3 has no run-length form
             bm.query_run(pool, dg.Query(np.array([0, 3]), 0, theta=1), out, path=bm.PATH_RLE)
         assert e.value.code == bm.BM_ERANGE
-        with pytest.raises(bm.BMError) as e:  # single queries only
-            bm.threshold_batch(pool, [dg.Query(np.array([0, 1]), 0, theta=1)], [out],
+        with pytest.raises(bm.BMError) as e:  # in a batch as well
+            bm.threshold_batch(pool, [dg.Query(np.array([0, 3]), 0, theta=1)], [out],
                                torch.zeros(1, dtype=torch.int64, device="cuda"), paths=[bm.PATH_RLE])
-        assert e.value.code == bm.BM_EINVAL
+        assert e.value.code == bm.BM_ERANGE
         with pytest.raises(bm.BMError):
             pool.rle_info(3)
