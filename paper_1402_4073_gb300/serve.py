@@ -18,7 +18,12 @@ BM_OK, BM_EBUSY = 0, -6
 
 
 class Server:
-    def __init__(self, pool, mem_budget: int, max_batch: int = 1024, max_inflight: int = 2,
+    """The native serving loop over `pool` (bm_server_*).  Under overload,
+    larger batches share each slab of the pool among more queries, so the
+    default allows two batches of up to 2048 requests in flight; below
+    saturation batches stay small and latency does not depend on it."""
+
+    def __init__(self, pool, mem_budget: int, max_batch: int = 2048, max_inflight: int = 2,
                  max_queue: int = 1 << 20, batch_window_us: int = 0):
         cfg = _native.bm_server_config(mem_budget, max_batch, max_inflight, max_queue,
                                        batch_window_us)
