@@ -422,9 +422,9 @@ int bm_server_destroy(bm_server* server);
 
 /*
  * Submit a query (its out_words is ignored: the result lives in a server
- * slot).  The query is copied; ids are validated at once (BM_EINVAL,
- * BM_ERANGE).  BM_EBUSY when max_queue requests already wait.  *ticket
- * identifies the request.
+ * slot) on any path bm_threshold_batch takes.  The query is copied; ids are
+ * validated at once for its path (BM_EINVAL, BM_ERANGE).  BM_EBUSY when
+ * max_queue requests already wait.  *ticket identifies the request.
  */
 int bm_server_submit(bm_server* server, const bm_query* q, uint64_t* ticket);
 

@@ -280,7 +280,7 @@ int bm_server_submit_deadline(bm_server* s, const bm_query* q, uint64_t deadline
                               uint64_t* ticket) {
     if (!s || !q || !ticket || !q->ids || q->n == 0 || q->n > BM_N_MAX || q->reserved)
         return BM_EINVAL;
-    if (q->kind > BM_KIND_TABLE || q->path < BM_PATH_AUTO || q->path > BM_PATH_SPARSE)
+    if (q->kind > BM_KIND_TABLE || q->path < BM_PATH_AUTO || q->path > BM_PATH_RLE)
         return BM_EINVAL;
     if (q->kind == BM_KIND_TABLE && !q->table) return BM_EINVAL;
     {

@@ -161,3 +161,32 @@ def test_cancel_and_deadline(bm, served):
         srv.release(t_keep)
         st = srv.stats()
         assert st["cancelled"] == 1 and st["expired"] == 1 and st["free_slots"] == 1
+
+
+def test_run_length_requests(bm, oracle_lib, dg):
+    """Requests on the run-length path are served with the oracle's answers,
+    beside one that BM_PATH_AUTO routes; one for an id without a run-length
+    form is refused at submission."""
+    from paper_1402_4073_gb300.serve import Server
+    r_bits = (1 << 20) + 3
+    words = dg.runs(dg.STREAM_TESTS + 15100, r_bits, np.linspace(0.01, 0.3, 32), 4096.0)
+    with bm.Pool(r_bits, 33) as pool:
+        pool.put_dense(words)
+        pool.put_rle(0, 32)
+        qs = [dg.Query(np.arange(32, dtype=np.uint32), 0, theta=3),
+              dg.Query(np.arange(5, 25, dtype=np.uint32), 1, lo=2, hi=6),
+              dg.Query(np.arange(0, 32, 3, dtype=np.uint32), 0, theta=2)]
+        paths = [bm.PATH_RLE, bm.PATH_RLE, None]
+        with Server(pool, mem_budget=_slots(pool, 8), max_batch=4, max_inflight=2) as srv:
+            tickets = [srv.submit(q, path=p) for q, p in zip(qs, paths)]
+            for t, q, p in zip(tickets, qs, paths):
+                assert srv.wait(t, 20000) == 0
+                w, c, _, _, ran = srv.result(t)
+                want = oracle_lib.query(words, q, r_bits)
+                assert np.array_equal(w, want[0]) and c == want[1]
+                if p is not None:
+                    assert ran == p
+                srv.release(t)
+            with pytest.raises(bm.BMError) as e:
+                srv.submit(dg.Query(np.array([0, 32], dtype=np.uint32), 0, theta=1), path=bm.PATH_RLE)
+            assert e.value.code == bm.BM_ERANGE
