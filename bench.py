@@ -147,20 +147,39 @@ def dist_setup(backend: str):
 
 def cpu_sample_time(words, queries, r_bits, budget_s: float):
     """Time the oracle on a bounded prefix of words, grown until it takes
-    about budget_s seconds; returns (bytes per second, sample words, threads)."""
+    about budget_s seconds; returns (bytes per second, sample words, seconds,
+    the oracle's answers over that prefix)."""
     import oracle
     nw = 256
     while True:
         t0 = time.perf_counter()
-        for q in queries:
-            oracle.query(words, q, r_bits, 0, nw)
+        answers = [oracle.query(words, q, r_bits, 0, nw) for q in queries]
         dt = time.perf_counter() - t0
         if dt > budget_s / 4 or nw >= words.shape[1]:
             break
         nw = min(words.shape[1], nw * 4)
     rows = 64 * nw
     nbytes = sum(query_bytes(q.n, rows) for q in queries)
-    return nbytes / dt, nw, dt
+    return nbytes / dt, nw, dt, answers
+
+
+def oracle_check(bm, outs, cards, answers, nw, total_words):
+    """Compare the timed run's outputs with the oracle's answers over the
+    sampled prefix of nw words (and the cardinalities when the sample covers
+    every word)."""
+    cards_h = cards.cpu().numpy()
+    words_ok = all(np_equal(bm.to_numpy_words(o)[:nw], a[0]) for o, a in zip(outs, answers))
+    full = nw >= total_words
+    cards_ok = (not full) or all(int(c) == a[1] for c, a in zip(cards_h, answers))
+    return {"checked_vs_oracle": bool(words_ok and cards_ok and full),
+            "oracle_check": f"output words 0..{nw} of {total_words} of every query "
+                            f"{'equal' if words_ok else 'DIFFER'}; cardinalities "
+                            f"{('equal' if cards_ok else 'DIFFER') if full else 'not compared (prefix)'}"}
+
+
+def np_equal(a, b) -> bool:
+    import numpy as np
+    return bool(np.array_equal(a, b))
 
 
 def bench_batched(bm, datagen, passes: int = 2, small: bool = False, config: str = ""):
@@ -669,7 +688,7 @@ def run_reference(args):
     # one step = the four queries over a fixed prefix of words, sized so that
     # the whole run (warm-up + timed steps) takes about two minutes
     per_step_s = min(1.0, 120.0 / max(1, args.steps + args.warmup))
-    _, nw, dt = cpu_sample_time(words, queries, R_BITS, 2.0)
+    _, nw, dt, _ = cpu_sample_time(words, queries, R_BITS, 2.0)
     nw = max(64, int(nw * min(8.0, per_step_s / max(dt, 1e-3))))
     nw = min(nw, words.shape[1])
     for _ in range(args.warmup):
@@ -743,14 +762,13 @@ def main():
     stream = torch.cuda.current_stream()
     outs = [pool.empty_words() for _ in queries]
     cards = torch.zeros(len(queries), dtype=torch.int64, device="cuda")
-    tables = {i: bm.interval_table(q.n, q.lo, q.hi) for i, q in enumerate(queries) if q.kind == 1}
 
     def launch(i, q, out=None):
         o = outs[i] if out is None else out
         if q.kind == 0:
             bm.threshold(pool, q.ids, q.theta, o, cards[i:i + 1])
-        else:
-            bm.symmetric(pool, q.ids, tables[i], o, cards[i:i + 1])
+        else:  # BM_KIND_INTERVAL through bm_query_run
+            bm.interval(pool, q.ids, q.lo, q.hi, o, cards[i:i + 1])
 
     # kernel shape: the library's autotuner (results are identical for every shape)
     if args.dense_config:
@@ -805,7 +823,7 @@ def main():
     achieved = query_bytes(N, R_BITS) / avg_launch_s / 1e9
     peak, peak_src = peaks()
 
-    # end to end through the public API: host ids (and tables) in, every
+    # end to end through the public API: host ids in, every
     # output bitmap and cardinality copied back to pinned host memory every
     # step.  Each copy runs on a second stream after its query's kernel (an
     # event), so a query's result travels while the next query computes.
@@ -825,7 +843,7 @@ def main():
         if q.kind == 0:
             bm.threshold(pool, q.ids, q.theta, o, c)
         else:
-            bm.symmetric(pool, q.ids, tables[i], o, c)
+            bm.interval(pool, q.ids, q.lo, q.hi, o, c)
 
     e2e_steps = max(3, min(args.steps, 50))
     torch.cuda.synchronize()
@@ -852,20 +870,23 @@ def main():
     last = (e2e_steps - 1) % nbuf
     assert torch.equal(host_card[last], cards.cpu()), "end-to-end cardinalities differ"
     assert torch.equal(host_out[last][0], outs[0].cpu()), "end-to-end output differs"
-    h2d = sum(4 * q.n + (8 * len(tables[i]) if i in tables else 0) for i, q in enumerate(queries))
+    h2d = sum(4 * q.n for q in queries)
     d2h = nq * pool.words * 8 + nq * 8
     e2e = step_bytes * world / e2e_s / 1e9
 
     cpu = None
+    checked = {"checked_vs_oracle": False, "oracle_check": "not run"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
         oracle.set_threads(os.cpu_count() or 1)
-        bps, nw, dt = cpu_sample_time(words, queries, R_BITS, args.cpu_budget)
+        bps, nw, dt, answers = cpu_sample_time(words, queries, R_BITS, args.cpu_budget)
         cpu = {"value": round(bps / 1e9, 4), "unit": "GB/s", "cores": oracle_threads(),
                "kind": "oracle",
                "sample": f"the 4 queries over the first {nw} of {words.shape[1]} words "
                          f"({64 * nw} rows), {dt:.1f} s"}
+        # the oracle's answers of that sample against the timed run's outputs
+        checked = oracle_check(bm, outs, cards, answers, nw, words.shape[1])
 
     extra = {}
     parts = args.parts.split(",")
@@ -905,6 +926,7 @@ def main():
             "e2e": {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": nq * args.steps,
+            **checked,
             "clocks": clocks,
             **extra,
         }))

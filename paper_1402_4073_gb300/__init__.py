@@ -227,12 +227,25 @@ def cardinality(words: torch.Tensor, r_bits: int, out_card: torch.Tensor, stream
                              _stream(stream)), "bm_cardinality")
 
 
-def interval_table(n: int, lo: int, hi: int) -> np.ndarray:
-    """Truth table words of f(c) = [lo <= c <= hi], c = 0..n (argument marshalling)."""
-    t = np.zeros((n + 1 + 63) // 64, dtype=np.uint64)
-    for c in range(max(lo, 0), min(hi, n) + 1):
-        t[c // 64] |= np.uint64(1) << np.uint64(c % 64)
-    return t
+def interval(pool: Pool, ids, lo: int, hi: int, out_words: torch.Tensor,
+             out_card: torch.Tensor | None = None, path: int | None = None, stream=None) -> int:
+    """Interval query lo <= count <= hi (BM_KIND_INTERVAL: the library builds
+    T_lo AND NOT T_{hi+1}) on `path` (dense by default); returns the path
+    that ran."""
+    i = _host_u32(ids)
+    q = _native.bm_query()
+    q.ids = i.ctypes.data
+    q.n = len(i)
+    q.kind = KIND_INTERVAL
+    q.theta, q.lo, q.hi = 0, int(lo), int(hi)
+    q.table = None
+    q.out_words = _dev_ptr(out_words, 8 * pool.words)
+    q.path = PATH_DENSE if path is None else int(path)
+    q.reserved = 0
+    chosen = ctypes.c_int32()
+    check(lib.bm_query_run(pool.handle, ctypes.byref(q), _dev_ptr(out_card, 8),
+                           ctypes.byref(chosen), _stream(stream)), "bm_query_run")
+    return int(chosen.value)
 
 
 def to_numpy_words(t: torch.Tensor) -> np.ndarray:

@@ -40,7 +40,7 @@ def run_query(bm, pool, q):
     if q.kind == 0:
         bm.threshold(pool, q.ids, q.theta, out, card)
     elif q.kind == 1:
-        bm.symmetric(pool, q.ids, bm.interval_table(q.n, q.lo, q.hi), out, card)
+        bm.interval(pool, q.ids, q.lo, q.hi, out, card)
     else:
         bm.symmetric(pool, q.ids, q.table, out, card)
     torch.cuda.synchronize()
@@ -257,17 +257,25 @@ def config2_answers(oracle_lib, config2):
     return [oracle_lib.query(words, q, 1 << 26) for q in queries]
 
 
-@pytest.mark.parametrize("variant", VARIANTS[:2])
+@pytest.mark.parametrize("variant", VARIANTS[:2] + [VARIANTS[8], "tuned"])
 def test_config2_full_size(bm, config2, config2_answers, variant):
     """N=256, r=2^26: the whole output bitmap and its cardinality of every
-    query, against the oracle run over every word."""
+    query, against the oracle run over every word.  "tuned" runs the shape the
+    autotuner installs on this pool (the one the benchmark times); VARIANTS[8]
+    is the 32-input adder shape, where each thread walks several columns of
+    the grid-stride loop at this size."""
     words, queries = config2
     r_bits = 1 << 26
     with make_pool(bm, words, r_bits) as pool:
-        pool.set_dense_config(*variant)
+        if variant == "tuned":
+            report = pool.autotune()
+            what = f"tuned {pool.configs()['dense']} ({report})"
+        else:
+            pool.set_dense_config(*variant)
+            what = str(variant)
         for q, want in zip(queries, config2_answers):
             got = run_query(bm, pool, q)
-            check_equal(got, want, f"kind={q.kind} theta={q.theta}")
+            check_equal(got, want, f"{what} kind={q.kind} theta={q.theta}")
 
 
 def test_config2_full_size_looped(bm, config2, config2_answers):
