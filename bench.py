@@ -348,6 +348,7 @@ def bench_sparse(bm, datagen, reps: int = 20, small: bool = False, config: str =
     out = pool.empty_words()
     card = torch.zeros(1, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     rows = []
     for n in (1500, 537, 128, 16):
         ids = datagen.floyd(datagen.STREAM_SPARSE + (9 << 32) + n, nbm, n)
@@ -365,9 +366,12 @@ def bench_sparse(bm, datagen, reps: int = 20, small: bool = False, config: str =
         us = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(reps)) * 1e3
         b = int(lens[ids].sum())
         alg = 4 * b + r_bits // 8
+        cold, hot = call_times(lambda: pq.run(card), reps, flush)
         rows.append({"N": n, "positions": b, "us_per_query": round(us, 1),
                      "achieved_GBps": round(alg / us / 1e3, 1),
-                     "frac": round(alg / us / 1e3 / peak, 4)})
+                     "frac": round(alg / us / 1e3 / peak, 4),
+                     "cold_us": round(cold, 2), "cold_frac": round(alg / cold / 1e3 / peak, 4),
+                     "hot_us": round(hot, 2)})
     pool.status()
     pool.close()
     cos = bench_cosparse(bm, datagen, r_bits, nbm, reps, peak, config)
@@ -375,7 +379,8 @@ def bench_sparse(bm, datagen, reps: int = 20, small: bool = False, config: str =
                         "(densities log-uniform [1e-5,1e-2], position lists), theta=min(N,8)",
             "kernel": "ScanCount (scancount_kernel)", "bytes": "4 * positions + r/8 per query",
             "peak": peak, "peak_source": f"hbm_gbs of {peak_src}",
-            "timing": f"median of {reps} launches, CUDA events around each bm_query_run",
+            "timing": f"us_per_query: median of {reps} launches, CUDA events around each "
+                      "bm_query_run (host time inside); cold/hot: see the small part",
             "queries": rows, "autotune": tune, "co_sparse": cos}
 
 
@@ -512,6 +517,86 @@ def bench_rle(bm, datagen, reps: int = 10, small: bool = False):
             "peak": peak, "peak_source": f"hbm_gbs of {peak_src}",
             "timing": f"median of {reps} calls, CUDA events around each bm_query_run",
             "pools": pools}
+
+
+def call_times(call, reps: int, flush):
+    """Device time per call of `call` (one query through the C ABI):
+    cold = median over `reps` calls, each queued behind a write of `flush`
+    (larger than L2), so the interval between its events holds its GPU work
+    and no host gap; hot = mean over `reps` calls queued back to back behind
+    a sleep kernel (the per-call cost of a stream of calls).  Microseconds."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        call()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+    torch.cuda.synchronize()
+    for i in range(reps):
+        flush.fill_(i & 255)
+        ev[2 * i].record(stream)
+        call()
+        ev[2 * i + 1].record(stream)
+    torch.cuda.synchronize()
+    cold = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(reps)) * 1e3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda._sleep(4_000_000)  # about 2 ms: the host queues the calls meanwhile
+    e0.record(stream)
+    for _ in range(reps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return cold, e0.elapsed_time(e1) * 1e3 / reps
+
+
+def bench_small(bm, datagen, reps: int = 40):
+    """Launch-bound single queries: the plain dense workload (N = 16 bitmaps
+    of r = 2^20 rows, Bernoulli(0.1); theta = 3, theta = 8 and the interval
+    [2, 5]) and dense N = 16 and N = 64 over r = 2^24 rows (the same
+    density).  Per query, device time per call:
+      cold: L2 flushed before each call by writing a 256 MiB buffer (larger
+            than the 129 MB L2); the call is queued behind the flush, so the
+            interval between its events holds its GPU work and no host gap;
+      hot:  `reps` calls queued back to back behind a sleep kernel (inputs
+            stay in L2): the per-call cost of a stream of calls.
+    GB/s = (N r/8 + r/8) per call; the fraction is of the HBM copy peak."""
+    import numpy as np
+    import torch
+    peak, peak_src = peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    card = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cases = []
+    words1, queries1 = datagen.config1()
+    cases.append(("plain dense N=16 x r=2^20", 1 << 20, words1, queries1))
+    for n in (16, 64):
+        w = datagen.bernoulli(datagen.STREAM_CONFIG1 + (5 << 32) + n, 1 << 24, [0.1] * n)
+        cases.append((f"dense N={n} x r=2^24", 1 << 24, w,
+                      [datagen.Query(np.arange(n, dtype=np.uint32), 0, theta=3)]))
+    rows = []
+    for name, r_bits, words, queries in cases:
+        pool = bm.Pool(r_bits, words.shape[0])
+        pool.put_dense(words)
+        pool.autotune()
+        out = pool.empty_words()
+        for q in queries:
+            def call():
+                if q.kind == 0:
+                    bm.threshold(pool, q.ids, q.theta, out, card)
+                else:
+                    bm.interval(pool, q.ids, q.lo, q.hi, out, card)
+            cold, hot = call_times(call, reps, flush)
+            nbytes = query_bytes(q.n, r_bits)
+            rows.append({"case": name,
+                         "query": f"theta={q.theta}" if q.kind == 0 else f"[{q.lo},{q.hi}]",
+                         "cold_us": round(cold, 2), "hot_us": round(hot, 2),
+                         "cold_GBps": round(nbytes / cold / 1e3, 1),
+                         "cold_frac": round(nbytes / cold / 1e3 / peak, 4),
+                         "hot_GBps": round(nbytes / hot / 1e3, 1)})
+        pool.status()
+        pool.close()
+    return {"workload": "plain dense N=16 x r=2^20 (theta=3, 8, [2,5]); dense N=16, 64 x r=2^24",
+            "timing": f"cold: median of {reps} calls, each after a 256 MiB write (L2 flushed); "
+                      f"hot: {reps} calls back to back after a sleep kernel, mean",
+            "peak": peak, "peak_source": f"hbm_gbs of {peak_src}", "queries": rows}
 
 
 def bench_looped(bm, pool, queries, launch, cards, reps: int = 20):
@@ -728,14 +813,19 @@ def main():
                     help="rows = 2^r_log2 (smaller cases are for profiling only)")
     ap.add_argument("--dense-config", default="",
                     help="variant,threads,stages,ctas_per_sm[,adder]: skip the variant search")
-    ap.add_argument("--parts", default="dense,looped,sparse,rle,weighted,batch,selector,serving",
-                    help="comma list of dense, looped, sparse, rle, weighted, batch, selector, serving")
+    ap.add_argument("--parts", default="dense,small,looped,sparse,rle,weighted,batch,selector,serving",
+                    help="comma list of dense, small, looped, sparse, rle, weighted, batch, selector, "
+                         "serving")
     ap.add_argument("--sparse-config", default="",
                     help="tile_rows,threads,ctas_per_sm,unroll for the sparse part: skip tuning")
     ap.add_argument("--batch-config", default="",
                     help="ctas_per_sm,adder,words_per_thread for the batch part: skip tuning")
     ap.add_argument("--small", action="store_true",
                     help="scaled-down batch/selector/serving workloads (profiling only)")
+    ap.add_argument("--shard", default="none", choices=["none", "rows"],
+                    help="rows: under torchrun, split the rows of every bitmap across the ranks "
+                         "(strong scaling: one query's work shared by all GPUs, cardinalities "
+                         "summed by one all-reduce per step); the other parts are skipped")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     global R_BITS, WORKLOAD
@@ -757,8 +847,25 @@ def main():
     datagen.build()
 
     words, queries = datagen.config2(R_BITS, N)
-    pool = bm.Pool(R_BITS, N, device=local)
-    pool.put_dense(words)
+    shard_rows = args.shard == "rows"
+    if shard_rows:
+        # this rank's word-aligned slice of the rows of every bitmap
+        from paper_1402_4073_gb300.shard import ShardedPool, sum_cardinalities
+        spool = ShardedPool(R_BITS, N, rank=rank, world=world, device=local)
+        spool.put_dense(words)
+        pool = spool.pool
+        local_rows = spool.rows
+        args.parts = "dense"
+    else:
+        pool = bm.Pool(R_BITS, N, device=local)
+        pool.put_dense(words)
+        local_rows = R_BITS
+
+    def exchange(c):
+        """Row shards: the whole queries' cardinalities (one all-reduce)."""
+        if shard_rows and world > 1:
+            sum_cardinalities(c)
+
     stream = torch.cuda.current_stream()
     outs = [pool.empty_words() for _ in queries]
     cards = torch.zeros(len(queries), dtype=torch.int64, device="cuda")
@@ -804,6 +911,7 @@ def main():
             ev[s][2 * i].record(stream)
             launch(i, q)
             ev[s][2 * i + 1].record(stream)
+        exchange(cards)
     end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -816,11 +924,13 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         el_ms = float(t.item())
     step_bytes = sum(query_bytes(q.n, R_BITS) for q in queries)
-    value = step_bytes * args.steps * world / (el_ms / 1e3) / 1e9
+    # replicas: every rank ran the whole workload; row shards: all ranks together ran it once
+    units = 1 if shard_rows else world
+    value = step_bytes * args.steps * units / (el_ms / 1e3) / 1e9
     launch_ms = [ev[s][2 * i].elapsed_time(ev[s][2 * i + 1]) for s in range(args.steps)
                  for i in range(nq)]
     avg_launch_s = statistics.mean(launch_ms) / 1e3
-    achieved = query_bytes(N, R_BITS) / avg_launch_s / 1e9
+    achieved = query_bytes(N, local_rows) / avg_launch_s / 1e9
     peak, peak_src = peaks()
 
     # end to end through the public API: host ids in, every
@@ -859,6 +969,11 @@ def main():
             copy_stream.wait_event(done)
             with torch.cuda.stream(copy_stream):
                 host_out[b][i].copy_(e_outs[b][i], non_blocking=True)
+        if shard_rows and world > 1:
+            exchange(e_cards[b])
+            summed = torch.cuda.Event()
+            summed.record(stream)
+            copy_stream.wait_event(summed)
         with torch.cuda.stream(copy_stream):
             host_card[b].copy_(e_cards[b], non_blocking=True)
         copied[b] = torch.cuda.Event()
@@ -872,7 +987,7 @@ def main():
     assert torch.equal(host_out[last][0], outs[0].cpu()), "end-to-end output differs"
     h2d = sum(4 * q.n for q in queries)
     d2h = nq * pool.words * 8 + nq * 8
-    e2e = step_bytes * world / e2e_s / 1e9
+    e2e = step_bytes * units / e2e_s / 1e9
 
     cpu = None
     checked = {"checked_vs_oracle": False, "oracle_check": "not run"}
@@ -893,6 +1008,8 @@ def main():
     if "looped" in parts:
         extra["looped"] = bench_looped(bm, pool, queries, launch, cards)
     pool.close()
+    if "small" in parts:
+        extra["small"] = bench_small(bm, datagen)
     if "sparse" in parts:
         extra["sparse"] = bench_sparse(bm, datagen, small=args.small, config=args.sparse_config)
     if "rle" in parts:
@@ -911,9 +1028,13 @@ def main():
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(el_ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "scaling": "strong" if shard_rows else "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "r_bits": R_BITS, "queries_per_step": nq,
-                       "queries_per_s": round(nq * args.steps * world / (el_ms / 1e3), 1),
+                       "parallelism": (f"row shards x{world} ({local_rows} rows on rank 0), "
+                                       "cardinalities all-reduced every step") if shard_rows else
+                                      f"replicas x{world} (independent queries)",
+                       "queries_per_s": round(nq * args.steps * units / (el_ms / 1e3), 1),
                        "l2": "inputs (2.15 GB per query) larger than L2; no flush",
                        "dense_config": best, "autotune": tune_report},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -921,7 +1042,7 @@ def main():
                          "peak_source": f"hbm_gbs of {peak_src}",
                          "traffic": traffic_per_launch(),
                          "kernel": "csa dense (bit-sliced carry-save counter)",
-                         "algorithmic_bytes_per_launch": query_bytes(N, R_BITS)},
+                         "algorithmic_bytes_per_launch": query_bytes(N, local_rows)},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

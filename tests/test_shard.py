@@ -1,6 +1,8 @@
-"""Row sharding across ranks, on CPU with two gloo ranks: each rank answers
-the query on its rows (the oracle stands in for the per-rank GPU path); the
-gathered bitmap and the summed cardinality equal the whole-pool answer."""
+"""Host logic of row sharding, on CPU with two gloo ranks: the row ranges,
+the slicing of full-width bitmaps, the all-reduce of the cardinalities and
+the all-gather of the output.  The per-rank compute here is the oracle on
+the rank's slice, so that this runs without a GPU; tests/test_shard_gpu.py
+runs the same exchange around the library's kernels on each rank's shard."""
 from __future__ import annotations
 
 import os
