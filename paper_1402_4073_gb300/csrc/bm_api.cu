@@ -73,16 +73,21 @@ uint32_t complement_inputs(const bm_pool* p, const uint32_t* ids, uint32_t n) {
 }
 
 // Stage ids (and a table-mode truth table) and launch the chosen kernel.
+// A query of at most kInlineIds inputs whose predicate needs no table passes
+// its ids in the kernel's parameter block: nothing is copied to the device.
+// The cardinality is stored by the kernel itself through the staging slot's
+// header (no memset), so such a query is one launch.
 int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<uint8_t>& f,
                int path, uint32_t tile_rows, uint64_t* out_words, uint64_t* out_card,
                cudaStream_t s) {
     Pred pred = compile_pred(f.data(), n);
-    const size_t ids_bytes = ((size_t)n * 4 + 15) & ~(size_t)15;
+    const bool inl = pred.mode != 2 && n <= kInlineIds;
+    const size_t ids_bytes = inl ? 0 : ((size_t)n * 4 + 15) & ~(size_t)15;
     const size_t tab_bytes = pred.mode == 2 ? (size_t)pred.table_words32 * 4 : 0;
     bm_stage_slot* sl = nullptr;
-    int rc = stage_acquire(p, ids_bytes + tab_bytes, &sl);
+    int rc = stage_acquire(p, ids_bytes + tab_bytes, &sl, s);
     if (rc) return rc;
-    memcpy(sl->h, ids, (size_t)n * 4);
+    if (!inl) memcpy(sl->h, ids, (size_t)n * 4);
     if (tab_bytes) {
         uint32_t* t = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(sl->h) + ids_bytes);
         memset(t, 0, tab_bytes);
@@ -90,10 +95,18 @@ int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<ui
             if (f[c]) t[c >> 5] |= 1u << (c & 31);
         pred.table = reinterpret_cast<const uint32_t*>(static_cast<uint8_t*>(sl->d) + ids_bytes);
     }
-    rc = stage_commit(sl, ids_bytes + tab_bytes, s);
-    if (rc) return rc;
-    if (out_card) BM_CUDA_TRY(cudaMemsetAsync(out_card, 0, 8, s));
-    const uint32_t* d_ids = static_cast<const uint32_t*>(sl->d);
+    if (ids_bytes + tab_bytes) {
+        rc = stage_commit(sl, ids_bytes + tab_bytes, s);
+        if (rc) return rc;
+    }
+    const uint32_t* d_ids = inl ? nullptr : static_cast<const uint32_t*>(sl->d);
+    unsigned long long* acc = out_card ? sl->acc() : nullptr;
+    LaunchExtra x{};
+    x.acc = acc;
+    x.ticket = sl->ticket();
+    x.n_inline = inl ? n : 0u;
+    if (inl) memcpy(x.inl, ids, (size_t)n * 4);
+    unsigned long long* card = reinterpret_cast<unsigned long long*>(out_card);
     if (path == BM_PATH_SPARSE) {
         SparseArgs a{};
         a.positions = p->d_pos;
@@ -107,8 +120,8 @@ int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<ui
         a.d_fill = complement_inputs(p, ids, n);
         a.pred = pred;
         a.out = out_words;
-        a.card = reinterpret_cast<unsigned long long*>(out_card);
-        rc = launch_sparse(a, p->sparse_cfg, p->sm_count, s);
+        a.card = card;
+        rc = launch_sparse(a, x, p->sparse_cfg, p->sm_count, s);
     } else if (path == BM_PATH_RLE) {
         RleArgs a{};
         a.runs = p->d_runs;
@@ -124,8 +137,8 @@ int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<ui
         a.n = n;
         a.pred = pred;
         a.out = out_words;
-        a.card = reinterpret_cast<unsigned long long*>(out_card);
-        rc = launch_rle(a, p->sm_count, s);
+        a.card = card;
+        rc = launch_rle(a, x, p->sm_count, s);
     } else {
         DenseArgs a{};
         a.base = p->d_dense;
@@ -136,13 +149,13 @@ int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<ui
         a.n = n;
         a.pred = pred;
         a.out = out_words;
-        a.card = reinterpret_cast<unsigned long long*>(out_card);
         a.err = p->d_err;
+        a.card = card;
         LoopedForm lf{};
         if (looped_form(pred, n, p->looped_max, &lf))
-            rc = launch_looped(a, lf, p->sm_count, s);
+            rc = launch_looped(a, x, lf, p->sm_count, s);
         else
-            rc = launch_dense(a, p->dense_cfg, p->sm_count, s);
+            rc = launch_dense(a, x, p->dense_cfg, p->sm_count, s);
     }
     int rc2 = stage_release(sl, s);
     return rc ? rc : rc2;

@@ -143,7 +143,9 @@ __device__ __forceinline__ unsigned long long sparse_item(const QueryDesc* d, co
     const uint32_t sub = tile_rows / kListTileRows;
     const uint64_t t0 = tile * sub;
     const uint64_t t1 = (t0 + sub < pa.tiles_per_list) ? t0 + sub : (uint64_t)pa.tiles_per_list;
-    count_tile<BITS, kSparseBatchUnroll>(cnt, scratch, s_next, d->ids, n,
+    const uint32_t* ids = d->ids;
+    count_tile<BITS, kSparseBatchUnroll>(cnt, scratch, s_next,
+                                         [ids](uint32_t j) { return __ldg(ids + j); }, n,
                                          reinterpret_cast<const uint4*>(pa.positions),
                                          pa.list_begin, pa.tile_index, pa.tiles_per_list, t0, t1,
                                          (uint32_t)rlo, (uint32_t)(rhi - rlo),
@@ -643,7 +645,8 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
         a.pred = hd[i].pred;  // a table, if any, in the descriptor block
         a.out = q[i].out_words;
         a.card = reinterpret_cast<unsigned long long*>(out_cards + i);
-        rc = launch_rle(a, p->sm_count, s);
+        const LaunchExtra none{};  // ids staged; the graph zeroed the cardinality
+        rc = launch_rle(a, none, p->sm_count, s);
         if (rc) return rc;
     }
     BM_CUDA_TRY(cudaEventRecord(sl.ev, s));

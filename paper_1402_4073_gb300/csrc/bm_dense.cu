@@ -44,8 +44,11 @@ __device__ __forceinline__ void load_table(const DenseArgs& a, uint32_t* tab, in
 // variant 0: direct streaming loads
 
 template <int K, int G, int L>
-__global__ void __launch_bounds__(256, (K <= 13 ? 2 : 1)) csa_direct_kernel(DenseArgs a) {
+__global__ void __launch_bounds__(256, (K <= 13 ? 2 : 1))
+    csa_direct_kernel(DenseArgs a, const __grid_constant__ LaunchExtra x) {
     extern __shared__ uint32_t tab[];
+    __shared__ __align__(16) uint32_t s_ids[kInlineIds];
+    const uint32_t* ids = launch_ids(a.ids, x, s_ids);
     load_table(a, tab, threadIdx.x, blockDim.x);
     __syncthreads();
     constexpr uint64_t W = L / 2;  // 64-bit words per thread per input
@@ -56,22 +59,25 @@ __global__ void __launch_bounds__(256, (K <= 13 ? 2 : 1)) csa_direct_kernel(Dens
          col += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t P[L][K];
         zero_planes<K, L>(P);
-        count_column<K, G, L>(P, a.base + W * col, a.ids, a.n, a.stride_words);
+        count_column<K, G, L, true>(P, a.base + W * col, ids, a.n, a.stride_words);
         card += finish_column<K, L>(P, a.pred, tab, a.r_bits, a.words, a.out, col, vec_ok);
     }
-    flush_card(card, a.card);
+    flush_card_block(card, a.card, x.acc, x.ticket);
 }
 
 // ---------------------------------------------------------------------------
 // variant 1: bulk-copy pipeline through shared memory
 
 template <int K, int NT>
-__global__ void __launch_bounds__(NT + 32, 1) csa_bulk_kernel(DenseArgs a, int stages) {
+__global__ void __launch_bounds__(NT + 32, 1)
+    csa_bulk_kernel(DenseArgs a, const __grid_constant__ LaunchExtra x, int stages) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint4* buf = reinterpret_cast<uint4*>(smem);  // [stages][16][NT]
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)stages * 16 * NT * 16);
     uint64_t* empty = full + stages;
     uint32_t* tab = reinterpret_cast<uint32_t*>(empty + stages);
+    __shared__ __align__(16) uint32_t s_ids[kInlineIds];
+    const uint32_t* ids = launch_ids(a.ids, x, s_ids);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int kConsumerWarps = NT / 32;
@@ -114,7 +120,7 @@ __global__ void __launch_bounds__(NT + 32, 1) csa_bulk_kernel(DenseArgs a, int s
                 __syncwarp();
                 if ((uint32_t)lane < nb) {
                     const uint8_t* src = reinterpret_cast<const uint8_t*>(a.base) +
-                                         (uint64_t)__ldg(a.ids + g * 16 + lane) * stride_bytes + off;
+                                         (uint64_t)ids[g * 16 + lane] * stride_bytes + off;
                     bulk_g2s(buf + ((size_t)s * 16 + lane) * NT, src, bytes, &full[s], pol);
                 }
                 __syncwarp();
@@ -163,11 +169,17 @@ __global__ void __launch_bounds__(NT + 32, 1) csa_bulk_kernel(DenseArgs a, int s
         if (col < ncols)
             card += finish_column<K, 4>(P, a.pred, tab, a.r_bits, a.words, a.out, col, vec_ok);
     }
-    if (ok) flush_card(card, a.card);
+    // every consumer warp contributes (nothing if its waits gave up, which
+    // the error word reports), so the last one completes the cardinality
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) card += __shfl_xor_sync(0xFFFFFFFFu, card, o);
+    if (lane == 0)
+        card_contribute(ok ? card : 0ull, a.card, x.acc, x.ticket, gridDim.x * kConsumerWarps);
 }
 
 template <int K>
-int launch_k(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStream_t s) {
+int launch_k(const DenseArgs& a, const LaunchExtra& x, const DenseConfig& cfg, int sm_count,
+             cudaStream_t s) {
     const uint64_t ncols = (a.words + 1) / 2;
     const size_t tab_bytes = a.pred.mode == 2 ? (size_t)a.pred.table_words32 * 4 : 0;
     if (cfg.variant == 0) {
@@ -185,7 +197,7 @@ int launch_k(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStrea
         if (tab_bytes > 48 * 1024)
             BM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)tab_bytes));
-        fn<<<grid, threads, tab_bytes, s>>>(a);
+        fn<<<grid, threads, tab_bytes, s>>>(a, x);
         BM_CUDA_TRY(cudaGetLastError());
         return BM_OK;
     }
@@ -203,7 +215,7 @@ int launch_k(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStrea
         const uint64_t ntiles = (ncols + nt - 1) / nt;
         const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);
         const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(ntiles, cap));
-        fn<<<grid, nt + 32, bytes, s>>>(a, stages);
+        fn<<<grid, nt + 32, bytes, s>>>(a, x, stages);
         BM_CUDA_TRY(cudaGetLastError());
         return BM_OK;
     };
@@ -214,13 +226,14 @@ int launch_k(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStrea
 
 }  // namespace
 
-int launch_dense(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStream_t s) {
+int launch_dense(const DenseArgs& a, const LaunchExtra& x, const DenseConfig& cfg, int sm_count,
+                 cudaStream_t s) {
     if (a.words == 0) return BM_OK;
     const int k = planes_for(a.n);
-    if (k <= 5) return launch_k<5>(a, cfg, sm_count, s);
-    if (k <= 9) return launch_k<9>(a, cfg, sm_count, s);
-    if (k <= 13) return launch_k<13>(a, cfg, sm_count, s);
-    return launch_k<17>(a, cfg, sm_count, s);
+    if (k <= 5) return launch_k<5>(a, x, cfg, sm_count, s);
+    if (k <= 9) return launch_k<9>(a, x, cfg, sm_count, s);
+    if (k <= 13) return launch_k<13>(a, x, cfg, sm_count, s);
+    return launch_k<17>(a, x, cfg, sm_count, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -77,12 +77,26 @@ __device__ __forceinline__ void zero_planes(uint32_t (&P)[L][K]) {
         for (int j = 0; j < K; ++j) P[l][j] = 0u;
 }
 
+// Four ids (16-byte aligned) and one id: read-only global loads, or, with
+// Gen, generic loads (ids that may sit in shared memory).
+template <bool Gen>
+__device__ __forceinline__ uint4 ld_ids4(const uint32_t* p) {
+    if constexpr (Gen) return *reinterpret_cast<const uint4*>(p);
+    else return __ldg(reinterpret_cast<const uint4*>(p));
+}
+template <bool Gen>
+__device__ __forceinline__ uint32_t ld_id(const uint32_t* p) {
+    if constexpr (Gen) return *p;
+    else return __ldg(p);
+}
+
 // Count one column (L lanes of 32 rows) of the n inputs ids[0..n) with
 // direct streaming loads, G (32, 16 or 8) inputs per sideways-sum block.  ids
 // must be 16-byte aligned: full blocks read their ids four at a time.  The
 // last n mod G inputs go through 8-input blocks padded with zero inputs,
-// which costs less than rippling each input through every plane.
-template <int K, int G, int L>
+// which costs less than rippling each input through every plane.  Gen: ids
+// are read with generic loads (they may be in shared memory).
+template <int K, int G, int L, bool Gen = false>
 __device__ __forceinline__ void count_column(uint32_t (&P)[L][K], const uint64_t* colbase,
                                              const uint32_t* ids, uint32_t n,
                                              uint64_t stride_words) {
@@ -96,7 +110,7 @@ __device__ __forceinline__ void count_column(uint32_t (&P)[L][K], const uint64_t
                 uint32_t id[16];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const uint4 q = __ldg(reinterpret_cast<const uint4*>(ids + k + 16 * h) + i);
+                    const uint4 q = ld_ids4<Gen>(ids + k + 16 * h + 4 * i);
                     id[4 * i] = q.x;
                     id[4 * i + 1] = q.y;
                     id[4 * i + 2] = q.z;
@@ -123,7 +137,7 @@ __device__ __forceinline__ void count_column(uint32_t (&P)[L][K], const uint64_t
         uint32_t id[GB];
 #pragma unroll
         for (int i = 0; i < GB / 4; ++i) {
-            const uint4 q = __ldg(reinterpret_cast<const uint4*>(ids + k) + i);
+            const uint4 q = ld_ids4<Gen>(ids + k + 4 * i);
             id[4 * i] = q.x;
             id[4 * i + 1] = q.y;
             id[4 * i + 2] = q.z;
@@ -140,7 +154,7 @@ __device__ __forceinline__ void count_column(uint32_t (&P)[L][K], const uint64_t
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
             if ((uint32_t)b < m) {
-                v[b] = ld_slice<L>(colbase + (uint64_t)__ldg(ids + k + b) * stride_words);
+                v[b] = ld_slice<L>(colbase + (uint64_t)ld_id<Gen>(ids + k + b) * stride_words);
             } else {
 #pragma unroll
                 for (int l = 0; l < L; ++l) v[b].v[l] = 0u;

@@ -175,6 +175,59 @@ __device__ __forceinline__ uint32_t eval_pred(const uint32_t (&P)[K], const Pred
     return r;
 }
 
+// --- ids and cardinality of a single-query launch ---------------------------
+
+// The ids of the launch: a query of at most kInlineIds inputs carries them in
+// the parameter block, and each CTA copies them to `s_ids` (the caller
+// synchronises the block before reading them); otherwise the staged device
+// copy.  Reads through the returned pointer are generic loads.
+__device__ __forceinline__ const uint32_t* launch_ids(const uint32_t* ids, const LaunchExtra& x,
+                                                      uint32_t* s_ids) {
+    if (x.n_inline == 0) return ids;
+    for (uint32_t i = threadIdx.x; i < x.n_inline; i += blockDim.x) s_ids[i] = x.inl[i];
+    return s_ids;
+}
+
+// One contributor's part of the cardinality.  With acc null the part is
+// added to *out (zeroed by the caller).  Otherwise the part is added to *acc
+// and an arrival counted on *ticket; the last of `contributors` arrivals
+// (fences order every part before it) stores the total to *out and returns
+// acc and ticket to zero for the next launch that uses them, so *out needs no
+// clearing beforehand and the launch needs no separate memset.
+__device__ __forceinline__ void card_contribute(unsigned long long part, unsigned long long* out,
+                                                unsigned long long* acc, unsigned int* ticket,
+                                                uint32_t contributors) {
+    if (!acc) {
+        if (out && part) atomicAdd(out, part);
+        return;
+    }
+    if (part) atomicAdd(acc, part);
+    __threadfence();
+    if (atomicAdd(ticket, 1u) == contributors - 1u) {
+        __threadfence();
+        const unsigned long long total = atomicExch(acc, 0ull);
+        atomicExch(ticket, 0u);
+        if (out) *out = total;
+    }
+}
+
+// Block-wide sum of every thread's count, then one contribution per CTA
+// (contributors = the grid's CTAs).  Every thread of the block calls it.
+__device__ __forceinline__ void flush_card_block(unsigned long long card, unsigned long long* out,
+                                                 unsigned long long* acc, unsigned int* ticket) {
+    __shared__ unsigned long long s_part[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) card += __shfl_xor_sync(0xFFFFFFFFu, card, o);
+    const uint32_t warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) s_part[warp] = card;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (uint32_t w = 0; w < nwarps; ++w) t += s_part[w];
+        card_contribute(t, out, acc, ticket, gridDim.x);
+    }
+}
+
 // --- time, loads ------------------------------------------------------------
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;

@@ -59,6 +59,11 @@ Pred compile_pred(const uint8_t* f, uint32_t n);
 void threshold_truth(uint32_t n, uint32_t theta, std::vector<uint8_t>& f);
 void interval_truth(uint32_t n, uint32_t lo, uint32_t hi, std::vector<uint8_t>& f);
 
+// Ids of a query of at most kInlineIds inputs travel in the kernel's
+// parameter block (copied to shared memory by each CTA) instead of a staged
+// host-to-device copy: a small query is then a single launch.
+constexpr uint32_t kInlineIds = 256;
+
 // Arguments of one dense query launch.
 struct DenseArgs {
     const uint64_t* base;     // pool dense storage
@@ -69,8 +74,19 @@ struct DenseArgs {
     uint32_t n;
     Pred pred;
     uint64_t* out;            // device, `words` words
-    unsigned long long* card; // device, pre-zeroed accumulator (may be null)
+    unsigned long long* card; // device cardinality (may be null): a pre-zeroed
+                              // accumulator, or, with LaunchExtra::acc, stored
     int* err;                 // device error word
+};
+
+// Second parameter of the single-query kernels: a small query's ids inline
+// and the cardinality's completion state.
+struct LaunchExtra {
+    unsigned long long* acc;  // device, zero on entry and on exit (null: card is
+                              // a pre-zeroed accumulator that the kernel adds to)
+    unsigned int* ticket;     // device, zero on entry and on exit (with acc)
+    uint32_t n_inline;        // ids in inl[] (the Args' ids pointer is then unused), else 0
+    uint32_t inl[kInlineIds];
 };
 
 // Dense kernel variants (the autotuner picks one per shape).
@@ -83,7 +99,8 @@ struct DenseConfig {
     int words_per_thread = 2;  // 64-bit words per thread per input: 2 or 1 (variant 0)
 };
 
-int launch_dense(const DenseArgs& a, const DenseConfig& cfg, int sm_count, cudaStream_t s);
+int launch_dense(const DenseArgs& a, const LaunchExtra& x, const DenseConfig& cfg, int sm_count,
+                 cudaStream_t s);
 
 // The Looped recurrence (Sec. 4.4) for a plain threshold whose T, or whose
 // complement N - T + 1 (Sec. 2.3, corrected), is at most kLoopedMaxT.
@@ -95,7 +112,8 @@ struct LoopedForm {
 };
 // True (and *form set) if pred over n inputs is such a threshold with t <= max_t.
 bool looped_form(const Pred& pred, uint32_t n, uint32_t max_t, LoopedForm* form);
-int launch_looped(const DenseArgs& a, const LoopedForm& f, int sm_count, cudaStream_t s);
+int launch_looped(const DenseArgs& a, const LaunchExtra& x, const LoopedForm& f, int sm_count,
+                  cudaStream_t s);
 
 // Arguments of one sparse (ScanCount) query launch.
 struct SparseArgs {
@@ -110,7 +128,7 @@ struct SparseArgs {
     uint32_t d_fill;             // inputs given by their zeros: the counters' start value
     Pred pred;
     uint64_t* out;
-    unsigned long long* card;
+    unsigned long long* card;    // as DenseArgs
 };
 
 struct SparseConfig {
@@ -120,7 +138,8 @@ struct SparseConfig {
     int unroll = 4;      // list slices a warp has in flight: 4 or 8
 };
 
-int launch_sparse(const SparseArgs& a, const SparseConfig& cfg, int sm_count, cudaStream_t s);
+int launch_sparse(const SparseArgs& a, const LaunchExtra& x, const SparseConfig& cfg, int sm_count,
+                  cudaStream_t s);
 
 // Word-aligned run-length form of a bitmap (EWAH-like, Sec. 2.1): maximal
 // runs of all-zero words, all-one words or literal words.  A run is a uint2:
@@ -147,10 +166,10 @@ struct RleArgs {
     uint32_t n;
     Pred pred;
     uint64_t* out;
-    unsigned long long* card;
+    unsigned long long* card;    // as DenseArgs
 };
 
-int launch_rle(const RleArgs& a, int sm_count, cudaStream_t s);
+int launch_rle(const RleArgs& a, const LaunchExtra& x, int sm_count, cudaStream_t s);
 // Run-length encoding of `words` words (host): runs (with the sentinel),
 // literal words, and the summary of every kRleTileWords-word tile (tiles + 1
 // entries): index of the run holding its first word | class << 30, the class
@@ -164,12 +183,23 @@ int planes_for(uint32_t n);  // counter planes needed for counts 0..n
 }  // namespace bm
 
 // Per-call host->device staging: pinned host block + device block + event.
+// The device block starts with a header of kStageHeader bytes that is never
+// copied over: the cardinality accumulator (uint64) and the arrival ticket
+// (uint32) of the call's kernel (see CardOut in bm_device.cuh), zero between
+// calls; h and d point past it, at the staged payload.
+constexpr size_t kStageHeader = 16;
 struct bm_stage_slot {
-    void* h = nullptr;
-    void* d = nullptr;
-    size_t cap = 0;
+    void* h = nullptr;       // payload, pinned host
+    void* d = nullptr;       // payload, device
+    void* h_base = nullptr;  // allocations
+    void* d_base = nullptr;
+    size_t cap = 0;          // payload bytes
     cudaEvent_t ev = nullptr;
     bool used = false;
+    unsigned long long* acc() const { return static_cast<unsigned long long*>(d_base); }
+    unsigned int* ticket() const {
+        return reinterpret_cast<unsigned int*>(static_cast<uint8_t*>(d_base) + 8);
+    }
 };
 
 struct bm_pool {
@@ -228,8 +258,9 @@ int query_truth(const bm_query* q, std::vector<uint8_t>& f);
 int validate_ids(const bm_pool* p, const uint32_t* ids, uint32_t n, int path);
 // Inputs of ids[0..n) whose position list holds their zeros (with repeats).
 uint32_t complement_inputs(const bm_pool* p, const uint32_t* ids, uint32_t n);
-// Reserve a staging slot of at least `bytes`, waiting for its previous use.
-int stage_acquire(bm_pool* p, size_t bytes, bm_stage_slot** out);
+// Reserve a staging slot of at least `bytes` of payload, waiting for its
+// previous use; a new device block gets its header zeroed on stream `s`.
+int stage_acquire(bm_pool* p, size_t bytes, bm_stage_slot** out, cudaStream_t s);
 // Copy the slot's first `bytes` to the device on `s` and mark its reuse point.
 int stage_commit(bm_stage_slot* slot, size_t bytes, cudaStream_t s);
 int stage_release(bm_stage_slot* slot, cudaStream_t s);

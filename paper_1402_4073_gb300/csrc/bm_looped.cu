@@ -34,8 +34,12 @@ __device__ __forceinline__ void looped_step(uint32_t (&A)[T], uint32_t x) {
 }
 
 template <int T, bool NEG>
-__global__ void __launch_bounds__(256, 2) looped_kernel(DenseArgs a, uint32_t flip) {
+__global__ void __launch_bounds__(256, 2)
+    looped_kernel(DenseArgs a, const __grid_constant__ LaunchExtra x, uint32_t flip) {
     constexpr int L = 4;        // 32-bit lanes per thread (two 64-bit words)
+    __shared__ __align__(16) uint32_t s_ids[kInlineIds];
+    const uint32_t* ids = launch_ids(a.ids, x, s_ids);
+    __syncthreads();
     const uint64_t ncols = (a.words + 1) / 2;
     const bool vec_ok = ((reinterpret_cast<uintptr_t>(a.out) & 15u) == 0);
     unsigned long long card = 0;
@@ -52,7 +56,7 @@ __global__ void __launch_bounds__(256, 2) looped_kernel(DenseArgs a, uint32_t fl
             uint32_t id[16];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const uint4 q = __ldg(reinterpret_cast<const uint4*>(a.ids + k) + i);
+                const uint4 q = ld_ids4<true>(ids + k + 4 * i);
                 id[4 * i] = q.x;
                 id[4 * i + 1] = q.y;
                 id[4 * i + 2] = q.z;
@@ -73,7 +77,7 @@ __global__ void __launch_bounds__(256, 2) looped_kernel(DenseArgs a, uint32_t fl
             Slice<L> v[8];
 #pragma unroll
             for (int b = 0; b < 8; ++b)
-                if ((uint32_t)b < m) v[b] = ld_slice<L>(colbase + (uint64_t)__ldg(a.ids + k + b) * a.stride_words);
+                if ((uint32_t)b < m) v[b] = ld_slice<L>(colbase + (uint64_t)ids[k + b] * a.stride_words);
 #pragma unroll
             for (int b = 0; b < 8; ++b)
                 if ((uint32_t)b < m)
@@ -109,15 +113,15 @@ __global__ void __launch_bounds__(256, 2) looped_kernel(DenseArgs a, uint32_t fl
             card += (unsigned long long)__popcll(w[0]);
         }
     }
-    flush_card(card, a.card);
+    flush_card_block(card, a.card, x.acc, x.ticket);
 }
 
 template <int T, bool NEG>
-int launch_t(const DenseArgs& a, uint32_t flip, int sm_count, cudaStream_t s) {
+int launch_t(const DenseArgs& a, const LaunchExtra& x, uint32_t flip, int sm_count, cudaStream_t s) {
     const uint64_t ncols = (a.words + 1) / 2;
     const uint64_t blocks = (ncols + 255) / 256;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(blocks, (uint64_t)sm_count * 2));
-    looped_kernel<T, NEG><<<grid, 256, 0, s>>>(a, flip);
+    looped_kernel<T, NEG><<<grid, 256, 0, s>>>(a, x, flip);
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
 }
@@ -138,16 +142,17 @@ bool looped_form(const Pred& pred, uint32_t n, uint32_t max_t, LoopedForm* form)
     return true;
 }
 
-int launch_looped(const DenseArgs& a, const LoopedForm& f, int sm_count, cudaStream_t s) {
+int launch_looped(const DenseArgs& a, const LaunchExtra& x, const LoopedForm& f, int sm_count,
+                  cudaStream_t s) {
     if (a.words == 0) return BM_OK;
     if (f.neg) {
-        if (f.t == 1) return launch_t<1, true>(a, f.flip, sm_count, s);
-        if (f.t == 2) return launch_t<2, true>(a, f.flip, sm_count, s);
-        return launch_t<3, true>(a, f.flip, sm_count, s);
+        if (f.t == 1) return launch_t<1, true>(a, x, f.flip, sm_count, s);
+        if (f.t == 2) return launch_t<2, true>(a, x, f.flip, sm_count, s);
+        return launch_t<3, true>(a, x, f.flip, sm_count, s);
     }
-    if (f.t == 1) return launch_t<1, false>(a, f.flip, sm_count, s);
-    if (f.t == 2) return launch_t<2, false>(a, f.flip, sm_count, s);
-    return launch_t<3, false>(a, f.flip, sm_count, s);
+    if (f.t == 1) return launch_t<1, false>(a, x, f.flip, sm_count, s);
+    if (f.t == 2) return launch_t<2, false>(a, x, f.flip, sm_count, s);
+    return launch_t<3, false>(a, x, f.flip, sm_count, s);
 }
 
 }  // namespace bm

@@ -34,7 +34,7 @@ void track_free(bm_pool* p, void* ptr, size_t bytes) {
     p->device_bytes -= std::min<uint64_t>(p->device_bytes, bytes);
 }
 
-int stage_acquire(bm_pool* p, size_t bytes, bm_stage_slot** out) {
+int stage_acquire(bm_pool* p, size_t bytes, bm_stage_slot** out, cudaStream_t s) {
     bm_stage_slot* sl = &p->slots[p->next_slot];
     p->next_slot = (p->next_slot + 1) % bm_pool::kSlots;
     if (sl->used) BM_CUDA_TRY(cudaEventSynchronize(sl->ev));  // previous call done with it
@@ -43,23 +43,26 @@ int stage_acquire(bm_pool* p, size_t bytes, bm_stage_slot** out) {
     bytes = std::max<size_t>(bytes, 256);
     if (sl->cap < bytes) {
         size_t cap = std::max(bytes, sl->cap * 2);
-        cap = (cap + 4095) & ~(size_t)4095;
-        if (sl->h) cudaFreeHost(sl->h);
-        track_free(p, sl->d, sl->cap);
-        sl->h = nullptr;
-        sl->d = nullptr;
+        cap = ((cap + kStageHeader + 4095) & ~(size_t)4095) - kStageHeader;
+        if (sl->h_base) cudaFreeHost(sl->h_base);
+        track_free(p, sl->d_base, sl->cap + kStageHeader);
+        sl->h = sl->d = sl->h_base = sl->d_base = nullptr;
         sl->cap = 0;
-        if (cudaHostAlloc(&sl->h, cap, cudaHostAllocDefault) != cudaSuccess) {
+        if (cudaHostAlloc(&sl->h_base, cap + kStageHeader, cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
-            sl->h = nullptr;
+            sl->h_base = nullptr;
             return BM_ENOMEM;
         }
-        int rc = track_alloc(p, &sl->d, cap);
+        int rc = track_alloc(p, &sl->d_base, cap + kStageHeader);
         if (rc) {
-            cudaFreeHost(sl->h);
-            sl->h = nullptr;
+            cudaFreeHost(sl->h_base);
+            sl->h_base = nullptr;
             return rc;
         }
+        // the header starts at zero; every kernel that uses it leaves it so
+        BM_CUDA_TRY(cudaMemsetAsync(sl->d_base, 0, kStageHeader, s));
+        sl->h = static_cast<uint8_t*>(sl->h_base) + kStageHeader;
+        sl->d = static_cast<uint8_t*>(sl->d_base) + kStageHeader;
         sl->cap = cap;
     }
     *out = sl;
@@ -230,8 +233,8 @@ int bm_pool_destroy(bm_pool* p) {
     batch_state_free(p);
     for (auto& sl : p->slots) {
         if (sl.ev) cudaEventDestroy(sl.ev);
-        if (sl.h) cudaFreeHost(sl.h);
-        if (sl.d) cudaFree(sl.d);
+        if (sl.h_base) cudaFreeHost(sl.h_base);
+        if (sl.d_base) cudaFree(sl.d_base);
     }
     if (p->d_dense) cudaFree(p->d_dense);
     if (p->d_err) cudaFree(p->d_err);
@@ -481,6 +484,10 @@ int bm_pool_status(bm_pool* p) {
     BM_CUDA_TRY(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         BM_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+        // a kernel that gave up may have left a cardinality header unfinished
+        for (auto& sl : p->slots)
+            if (sl.d_base) BM_CUDA_TRY(cudaMemset(sl.d_base, 0, kStageHeader));
+        BM_CUDA_TRY(cudaDeviceSynchronize());
         return BM_ETIMEOUT;
     }
     return BM_OK;

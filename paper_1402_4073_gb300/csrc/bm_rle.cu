@@ -165,7 +165,8 @@ __device__ __forceinline__ uint64_t eval_offset(const uint32_t (&P)[2][K], const
 }
 
 template <int K>
-__global__ void __launch_bounds__(kRleThreads, K <= 9 ? 4 : (K <= 13 ? 3 : 2)) rle_kernel(RleArgs a) {
+__global__ void __launch_bounds__(kRleThreads, K <= 9 ? 4 : (K <= 13 ? 3 : 2))
+    rle_kernel(RleArgs a, const __grid_constant__ LaunchExtra x) {
     extern __shared__ __align__(16) uint64_t sm64[];
     uint64_t* stage = sm64;                                                    // [kRleGroup][256]
     uint2* dirty = reinterpret_cast<uint2*>(stage + kRleGroup * kRleThreads);  // [kRleChunk]
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(kRleThreads, K <= 9 ? 4 : (K <= 13 ? 3 : 2)) r
 #pragma unroll
         for (uint32_t u = 0; u < kPer; ++u) {
             const uint32_t i = tid + u * kRleThreads;
-            id[u] = i < m ? __ldg(a.ids + c0 + i) : 0u;
+            id[u] = i >= m ? 0u : x.n_inline ? x.inl[c0 + i] : __ldg(a.ids + c0 + i);
         }
     };
     auto load_sums = [&](uint32_t m, uint64_t tile, uint32_t (&sum)[kPer]) {
@@ -307,11 +308,11 @@ __global__ void __launch_bounds__(kRleThreads, K <= 9 ? 4 : (K <= 13 ? 3 : 2)) r
         }
         __syncthreads();  // s_c1, s_nd, cov and warp_tot are reused by the next tile
     }
-    flush_card(card, a.card);
+    flush_card_block(card, a.card, x.acc, x.ticket);
 }
 
 template <int K>
-int launch_k(const RleArgs& a, int sm_count, cudaStream_t s) {
+int launch_k(const RleArgs& a, const LaunchExtra& x, int sm_count, cudaStream_t s) {
     const size_t tab_words = a.pred.mode == 2 ? (a.n + 1 + 31) / 32 : 0;
     const size_t smem = (size_t)kRleGroup * kRleThreads * 8 + (size_t)kRleChunk * 8 + tab_words * 4;
     BM_CUDA_TRY(
@@ -324,20 +325,20 @@ int launch_k(const RleArgs& a, int sm_count, cudaStream_t s) {
     const uint64_t ntiles = (a.words + kRleTileWords - 1) / kRleTileWords;
     const unsigned grid = (unsigned)std::max<uint64_t>(
         1, std::min<uint64_t>(ntiles, (uint64_t)sm_count * (uint64_t)std::max(1, per_sm)));
-    rle_kernel<K><<<grid, kRleThreads, smem, s>>>(a);
+    rle_kernel<K><<<grid, kRleThreads, smem, s>>>(a, x);
     BM_CUDA_TRY(cudaGetLastError());
     return BM_OK;
 }
 
 }  // namespace
 
-int launch_rle(const RleArgs& a, int sm_count, cudaStream_t s) {
+int launch_rle(const RleArgs& a, const LaunchExtra& x, int sm_count, cudaStream_t s) {
     if (a.words == 0) return BM_OK;
     const int k = planes_for(a.n);
-    if (k <= 5) return launch_k<5>(a, sm_count, s);
-    if (k <= 9) return launch_k<9>(a, sm_count, s);
-    if (k <= 13) return launch_k<13>(a, sm_count, s);
-    return launch_k<17>(a, sm_count, s);
+    if (k <= 5) return launch_k<5>(a, x, sm_count, s);
+    if (k <= 9) return launch_k<9>(a, x, sm_count, s);
+    if (k <= 13) return launch_k<13>(a, x, sm_count, s);
+    return launch_k<17>(a, x, sm_count, s);
 }
 
 }  // namespace bm

@@ -60,10 +60,11 @@ __device__ __forceinline__ void count_vec(uint32_t* cnt, const uint4& x, uint32_
 // identity of Sec. 2.3 applied input by input).  t0, t1: tile-index entries
 // bounding the tile.  vpos: the pool's list arena as 16-byte vectors.
 // scratch: kScanWarpWords shared words per warp.  s_next: a shared word.
+// id(j) returns the query's j-th id.
 // Every thread of the block calls this; it begins with a block barrier.
-template <int BITS, int U>
+template <int BITS, int U, typename IdOf>
 __device__ __forceinline__ void count_tile(uint32_t* cnt, uint32_t* scratch, uint32_t* s_next,
-                                           const uint32_t* ids, uint32_t n, const uint4* vpos,
+                                           IdOf id_of, uint32_t n, const uint4* vpos,
                                            const uint64_t* list_begin,
                                            const uint32_t* tile_index, uint32_t tiles_per_list,
                                            uint64_t t0, uint64_t t1, uint32_t lo,
@@ -87,7 +88,7 @@ __device__ __forceinline__ void count_tile(uint32_t* cnt, uint32_t* scratch, uin
         nv = 0u;
         const uint32_t j = g * 32 + lane;
         if (g < ngroups && j < n) {
-            const uint32_t id = __ldg(ids + j);
+            const uint32_t id = id_of(j);
             const uint32_t* idx = tile_index + (uint64_t)id * (tiles_per_list + 1);
             const uint32_t b = __ldg(idx + t0), en = __ldg(idx + t1);
             const uint64_t begin = __ldg(list_begin + id);

@@ -46,9 +46,12 @@ __device__ void build_truth(const Pred& pr, uint32_t n, uint32_t* tab, uint32_t 
 // Two 512-thread CTAs per SM: the pipelined loads need the 64 registers
 // that leaves.
 template <int BITS, int U>  // counter width: 8 or 16; pieces per load batch
-__global__ void __launch_bounds__(512, 2) scancount_kernel(SparseArgs a) {
+__global__ void __launch_bounds__(512, 2)
+    scancount_kernel(SparseArgs a, const __grid_constant__ LaunchExtra x) {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ uint32_t s_next;  // next group of lists to count
+    __shared__ __align__(16) uint32_t s_ids[kInlineIds];
+    launch_ids(a.ids, x, s_ids);
     constexpr uint32_t kPer = 32 / BITS;  // counters per 32-bit word
     const uint32_t tab_words = (a.n + 1 + 31) / 32;
     uint32_t* tab = sm;
@@ -57,7 +60,6 @@ __global__ void __launch_bounds__(512, 2) scancount_kernel(SparseArgs a) {
     const uint32_t cnt_words = a.tile_rows / kPer;
     build_truth(a.pred, a.n, tab, tab_words);
 
-    const uint32_t lane = threadIdx.x & 31;
     const uint64_t ntiles = (a.r_bits + a.tile_rows - 1) / a.tile_rows;
     const uint32_t sub = a.tile_rows / kListTileRows;  // index entries per tile
     unsigned long long card = 0;
@@ -69,7 +71,8 @@ __global__ void __launch_bounds__(512, 2) scancount_kernel(SparseArgs a) {
         const uint64_t hi = min(lo + a.tile_rows, a.r_bits);
         const uint64_t t0 = tile * sub;
         const uint64_t t1 = (t0 + sub < a.tiles_per_list) ? t0 + sub : (uint64_t)a.tiles_per_list;
-        count_tile<BITS, U>(cnt, scratch, &s_next, a.ids, a.n,
+        count_tile<BITS, U>(cnt, scratch, &s_next,
+                            [&](uint32_t j) { return x.n_inline ? s_ids[j] : __ldg(a.ids + j); }, a.n,
                             reinterpret_cast<const uint4*>(a.positions),
                             a.list_begin, a.tile_index, a.tiles_per_list, t0, t1, (uint32_t)lo,
                             (uint32_t)(hi - lo), a.tile_rows, a.d_fill);
@@ -89,14 +92,13 @@ __global__ void __launch_bounds__(512, 2) scancount_kernel(SparseArgs a) {
     // rows between r and the end of the last 64-bit word
     if (blockIdx.x == 0 && threadIdx.x == 0 && ((a.r_bits + 31) / 32) % 2 == 1)
         reinterpret_cast<uint32_t*>(a.out)[(a.r_bits + 31) / 32] = 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) card += __shfl_xor_sync(0xFFFFFFFFu, card, o);
-    if (lane == 0 && a.card && card) atomicAdd(a.card, card);
+    flush_card_block(card, a.card, x.acc, x.ticket);
 }
 
 }  // namespace
 
-int launch_sparse(const SparseArgs& a, const SparseConfig& cfg, int sm_count, cudaStream_t s) {
+int launch_sparse(const SparseArgs& a, const LaunchExtra& x, const SparseConfig& cfg, int sm_count,
+                  cudaStream_t s) {
     if (a.r_bits == 0) return BM_OK;
     // padded lists keep their padding out of every tile of at most 65536 rows
     if (a.tile_rows == 0 || a.tile_rows % kListTileRows || a.tile_rows > 65536) return BM_EINVAL;
@@ -118,7 +120,7 @@ int launch_sparse(const SparseArgs& a, const SparseConfig& cfg, int sm_count, cu
         if (smem > 48 * 1024)
             BM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem));
-        fn<<<grid, threads, smem, s>>>(b);
+        fn<<<grid, threads, smem, s>>>(b, x);
         BM_CUDA_TRY(cudaGetLastError());
         return BM_OK;
     };

@@ -98,5 +98,6 @@ extern "C" int bm_threshold_noalloc(const uint64_t* words, uint64_t stride_words
     a.card = reinterpret_cast<unsigned long long*>(out_card);
     a.err = nullptr;  // the direct-load kernel has no waits to report
     const bm::DenseConfig cfg{0, 256, 4, 2};
-    return bm::launch_dense(a, cfg, sm_count, s);
+    const bm::LaunchExtra none{};  // ids in the fixed array; out_card zeroed above
+    return bm::launch_dense(a, none, cfg, sm_count, s);
 }

@@ -191,7 +191,7 @@ extern "C" int bm_weighted_threshold(bm_pool* p, const bm_weighted_query* q, uin
     const size_t b1 = (ids1.size() * 4 + 15) & ~(size_t)15;
     const size_t bw = (idsw.size() * 4 + 15) & ~(size_t)15;
     bm_stage_slot* sl = nullptr;
-    rc = stage_acquire(p, b1 + 2 * bw + 16, &sl);
+    rc = stage_acquire(p, b1 + 2 * bw + 16, &sl, s);
     if (rc) return rc;
     uint8_t* h = static_cast<uint8_t*>(sl->h);
     if (!ids1.empty()) memcpy(h, ids1.data(), ids1.size() * 4);
