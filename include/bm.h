@@ -394,6 +394,8 @@ typedef struct bm_server_config {
     uint32_t max_inflight;    /* batches in flight at once, on as many streams (1..4) */
     uint32_t max_queue;       /* most requests waiting for admission; more: BM_EBUSY */
     uint32_t batch_window_us; /* pause before forming a batch, to let it grow (0: none) */
+    uint32_t slo_us;          /* latency objective (0: none), see bm_server_create */
+    uint32_t reserved;        /* must be 0 */
 } bm_server_config;
 
 typedef struct bm_server_stats_t {
@@ -414,6 +416,15 @@ typedef struct bm_server_stats_t {
  * output slot (one bitmap, ceil(r/64) words rounded to 256 bytes) is free;
  * slots come back when results are released.  BM_ENOMEM if the budget holds
  * no slot or cannot be allocated.
+ *
+ * Load shedding (slo_us > 0): the scheduler keeps running estimates of a
+ * batch's fixed time and of its time per request (from the batches it ran)
+ * and bounds every batch so that its oldest request can still complete
+ * within slo_us of its submission; a request that could not complete in time
+ * even in a batch of its own is dropped before it runs and completes as
+ * expired (BM_ETIMEOUT), as with a deadline.  Admitted requests therefore
+ * finish near or within the objective under overload instead of queueing
+ * without bound.  slo_us = 0 keeps batches of up to max_batch.
  */
 int bm_server_create(bm_pool* pool, const bm_server_config* cfg, bm_server** out);
 
@@ -466,7 +477,8 @@ int bm_server_release(bm_server* server, uint64_t ticket);
  * after the call starts (open loop, e.g. Poisson arrivals), collect every
  * result in order and release it.  Per request (host arrays of n entries,
  * each may be NULL): latency_us and queue_us as in bm_server_result, cards,
- * and status (BM_OK, BM_EBUSY when refused by admission, or an error).
+ * and status (BM_OK, BM_EBUSY when refused by admission, BM_ETIMEOUT when
+ * dropped by its deadline or the latency objective, or an error).
  * *wall_s: time from the first submission to the last collection.
  */
 int bm_server_replay(bm_server* server, const bm_query* qs, uint32_t n, const double* arrival_s,

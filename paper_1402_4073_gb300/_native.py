@@ -49,7 +49,7 @@ class bm_batch_config_t(ctypes.Structure):
 
 class bm_server_config(ctypes.Structure):
     _fields_ = [("mem_budget", u64), ("max_batch", u32), ("max_inflight", u32), ("max_queue", u32),
-                ("batch_window_us", u32)]
+                ("batch_window_us", u32), ("slo_us", u32), ("reserved", u32)]
 
 
 class bm_server_stats_t(ctypes.Structure):

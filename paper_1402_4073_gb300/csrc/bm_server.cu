@@ -43,6 +43,7 @@ struct Request {
 };
 
 struct Batch {
+    Clock::time_point t_launch;
     cudaStream_t stream = nullptr;
     uint64_t* d_cards = nullptr;
     uint64_t* h_cards = nullptr;  // pinned
@@ -71,6 +72,10 @@ struct bm_server {
     bool stop = false;
     std::thread th;
 
+    // running estimates of a batch's time: fixed part (from small batches)
+    // and time per request (from large ones), microseconds
+    double est_fixed_us = 100.0, est_per_req_us = 30.0;
+
     // statistics
     uint64_t submitted = 0, completed = 0, refused = 0, batches_run = 0, batched_queries = 0;
     uint64_t cancelled = 0, expired = 0;
@@ -94,6 +99,15 @@ void CUDART_CB on_batch_done(void* arg) {
             r->done = true;
         }
         s->completed += b->reqs.size();
+        // the batch's time updates the estimates the latency objective uses
+        const double exec = us_since(b->t_launch, now);
+        const double nb = (double)b->reqs.size();
+        if (nb <= 16) {
+            s->est_fixed_us = 0.9 * s->est_fixed_us + 0.1 * exec;
+        } else {
+            const double per = std::max(0.5, (exec - s->est_fixed_us) / nb);
+            s->est_per_req_us = 0.8 * s->est_per_req_us + 0.2 * per;
+        }
         b->reqs.clear();
         b->busy = false;
     }
@@ -139,11 +153,16 @@ void scheduler(bm_server* s) {
             if (s->stop) break;
         }
         {
-            // requests whose deadline passed while they waited complete as expired
+            // requests whose deadline passed while they waited complete as
+            // expired; with a latency objective, so do those that could not
+            // finish within it even in a batch of their own
             const auto now = Clock::now();
+            const auto slo = std::chrono::microseconds(s->cfg.slo_us);
+            const auto fixed = std::chrono::microseconds((int64_t)(s->est_fixed_us + s->est_per_req_us));
             bool expired = false;
             for (auto it = s->waiting.begin(); it != s->waiting.end();) {
-                if ((*it)->deadline <= now) {
+                if ((*it)->deadline <= now ||
+                    (s->cfg.slo_us && (*it)->t_submit + slo <= now + fixed)) {
                     Request* r = *it;
                     r->done = true;
                     r->t_launch = r->t_done = now;
@@ -159,9 +178,17 @@ void scheduler(bm_server* s) {
         }
         for (auto& b : s->batches) {
             if (b.busy || s->waiting.empty() || s->free_slots.empty()) continue;
+            // with a latency objective, the batch is sized so that its oldest
+            // request (the front) can still complete within it
+            size_t limit = s->cfg.max_batch;
+            if (s->cfg.slo_us) {
+                const double age = us_since(s->waiting.front()->t_submit, Clock::now());
+                const double budget = (double)s->cfg.slo_us - age - s->est_fixed_us;
+                const double fit = std::floor(budget / s->est_per_req_us);
+                limit = (size_t)std::max(1.0, std::min((double)limit, fit));
+            }
             std::vector<Request*> take;
-            while (!s->waiting.empty() && !s->free_slots.empty() &&
-                   take.size() < s->cfg.max_batch) {
+            while (!s->waiting.empty() && !s->free_slots.empty() && take.size() < limit) {
                 Request* r = s->waiting.front();
                 s->waiting.pop_front();
                 r->slot = s->free_slots.back();
@@ -173,6 +200,7 @@ void scheduler(bm_server* s) {
             b.reqs = take;
             b.busy = true;
             const auto now = Clock::now();
+            b.t_launch = now;
             std::vector<bm_query> qs(take.size());
             for (size_t i = 0; i < take.size(); ++i) {
                 take[i]->t_launch = now;
@@ -213,7 +241,7 @@ extern "C" {
 int bm_server_create(bm_pool* pool, const bm_server_config* cfg, bm_server** out) {
     if (!pool || !cfg || !out) return BM_EINVAL;
     if (cfg->max_batch == 0 || cfg->max_inflight == 0 || cfg->max_inflight > 4 ||
-        cfg->max_queue == 0)
+        cfg->max_queue == 0 || cfg->reserved)
         return BM_EINVAL;
     *out = nullptr;
     bm_pool_info_t info;
@@ -400,12 +428,20 @@ int bm_server_replay(bm_server* s, const bm_query* qs, uint32_t n, const double*
                 std::this_thread::sleep_for(std::chrono::microseconds(20));
             if (i >= submitted.load()) break;
             if (st[i] != BM_OK) continue;
-            // a request gets at most 10 s; after one expires the rest get 100 ms each
+            // a request gets at most 10 s; after one never completes the rest get 100 ms each
             int rc = bm_server_wait(s, tickets[i], stalled ? 100 : 10000);
             if (rc != BM_OK) {
-                if (rc == BM_ETIMEOUT) stalled = true;
+                double lat = 0, qu = 0;
                 st[i] = rc;
-                if (rc != BM_ETIMEOUT) bm_server_release(s, tickets[i]);
+                if (bm_server_result(s, tickets[i], nullptr, nullptr, &lat, &qu, nullptr) ==
+                    BM_ENOTREADY) {
+                    stalled = true;  // the wait itself ran out
+                    continue;
+                }
+                // completed without a result: dropped (deadline, objective) or failed
+                if (latency_us) latency_us[i] = lat;
+                if (queue_us) queue_us[i] = qu;
+                bm_server_release(s, tickets[i]);
                 continue;
             }
             double lat = 0, qu = 0;

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _native, _q_from, check, lib
 
-BM_OK, BM_EBUSY = 0, -6
+BM_OK, BM_ETIMEOUT, BM_EBUSY = 0, -5, -6
 
 
 class Server:
@@ -24,9 +24,12 @@ class Server:
     saturation batches stay small and latency does not depend on it."""
 
     def __init__(self, pool, mem_budget: int, max_batch: int = 2048, max_inflight: int = 2,
-                 max_queue: int = 1 << 20, batch_window_us: int = 0):
+                 max_queue: int = 1 << 20, batch_window_us: int = 0, slo_us: int = 0):
+        """slo_us > 0: load shedding by a latency objective (batches sized so
+        that their oldest request can still finish within slo_us; requests
+        that cannot are dropped as expired)."""
         cfg = _native.bm_server_config(mem_budget, max_batch, max_inflight, max_queue,
-                                       batch_window_us)
+                                       batch_window_us, slo_us, 0)
         h = ctypes.c_void_p()
         check(lib.bm_server_create(pool.handle, ctypes.byref(cfg), ctypes.byref(h)),
               "bm_server_create")
@@ -99,17 +102,27 @@ class Server:
                 "wall_s": wall.value}
 
 
-def summarize(res: dict, offered_qps: float) -> dict:
+def summarize(res: dict, offered_qps: float, slo_us: float | None = None) -> dict:
+    """Counts, achieved rate and latency percentiles of a replay; with
+    slo_us also the goodput (requests completed within slo_us per second)."""
     ok = res["status"] == BM_OK
     lat = res["latency_us"][ok]
     n_ok = int(ok.sum())
-    return {
+    out = {
         "offered_qps": offered_qps,
         "completed": n_ok,
         "refused": int((res["status"] == BM_EBUSY).sum()),
-        "errors": int(((res["status"] != BM_OK) & (res["status"] != BM_EBUSY)).sum()),
+        "expired": int((res["status"] == BM_ETIMEOUT).sum()),
+        "errors": int(((res["status"] != BM_OK) & (res["status"] != BM_EBUSY) &
+                       (res["status"] != BM_ETIMEOUT)).sum()),
         "achieved_qps": round(n_ok / res["wall_s"], 1) if res["wall_s"] > 0 else 0.0,
         "p50_us": round(float(np.percentile(lat, 50)), 1) if n_ok else None,
         "p99_us": round(float(np.percentile(lat, 99)), 1) if n_ok else None,
         "mean_queue_us": round(float(res["queue_us"][ok].mean()), 1) if n_ok else None,
     }
+    if slo_us:
+        good = int((lat <= slo_us).sum())
+        out["slo_us"] = round(float(slo_us), 1)
+        out["within_slo"] = good
+        out["goodput_qps"] = round(good / res["wall_s"], 1) if res["wall_s"] > 0 else 0.0
+    return out

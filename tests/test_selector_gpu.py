@@ -1,6 +1,10 @@
 """Learned selector: trained on the GPU by the library's own kernels from
 timings of the library's own kernels; results stay bit-exact whatever it
-picks; its time lost is compared with the fixed density rule's."""
+picks.  Its time lost (the paper's suboptimality summed over the workload)
+on held-out queries must be below the fixed density rule's and no worse than
+that of the best single fixed candidate; and the host-side inference that
+routes single queries must pick the argmin of the fp64 oracle network on the
+same standardised features."""
 from __future__ import annotations
 
 import numpy as np
@@ -24,19 +28,22 @@ def test_selector_trains_routes_and_stays_exact(bm, oracle_lib, dg):
     d = dg.pool_densities(dg.STREAM_TESTS + 14000, n_bm, 1e-5, 3e-2)
     words = dg.bernoulli(dg.STREAM_TESTS + 14001, r_bits, d)
     flat, offs = dg.positions(words, r_bits)
-    train_q = dg.sparse_queries(160, pool=n_bm, nmax=600, stream=dg.STREAM_TESTS + 14002)
-    test_q = dg.sparse_queries(80, pool=n_bm, nmax=600, stream=dg.STREAM_TESTS + 14003)
+    train_q = dg.sparse_queries(320, pool=n_bm, nmax=600, stream=dg.STREAM_TESTS + 14002)
+    test_q = dg.sparse_queries(240, pool=n_bm, nmax=600, stream=dg.STREAM_TESTS + 14003)
     with bm.Pool(r_bits, n_bm) as pool:
         pool.put_dense(words)
         pool.put_positions(flat, offs)
         ftr, ttr = selector.collect(pool, train_q, reps=3)
         fte, tte = selector.collect(pool, test_q, reps=3)
-        model = selector.train(ftr, ttr, steps=1500)
+        model = selector.train(ftr, ttr, steps=3000)
         res = selector.evaluate(pool, model, test_q, fte, tte)
-        print("selector:", res)
+        fixed = min(res[f"time_lost_always_c{c}"] for c in range(1, bm.SELECTOR_CANDIDATES))
+        fixed = min(fixed, res["time_lost_always_dense"])
+        print("selector:", res, "best fixed:", fixed)
         assert np.isfinite(model.final_loss)
-        assert res["time_lost_mlp"] <= res["time_lost_always_dense"] + 1e-9
-        assert res["time_lost_mlp"] <= res["time_lost_rule"] + 0.05
+        # what the trained network gains, on held-out queries
+        assert res["time_lost_mlp"] < res["time_lost_rule"], res
+        assert res["time_lost_mlp"] <= fixed, res
         # with the network installed, AUTO results are exact, single and batched
         selector.install(pool, model)
         outs = [pool.empty_words() for _ in test_q[:24]]
@@ -54,3 +61,55 @@ def test_selector_trains_routes_and_stays_exact(bm, oracle_lib, dg):
             assert np.array_equal(bm.to_numpy_words(o), want[0]) and int(c.item()) == want[1]
             assert path in (bm.PATH_DENSE, bm.PATH_SPARSE)
         assert set(chosen.tolist()) <= {bm.PATH_DENSE, bm.PATH_SPARSE}
+
+
+def _unpack(params, F=5, H=64, C=4):
+    """The flat fp32 parameter vector as the oracle's W1, b1, W2, b2, W3, b3."""
+    from oracle import mlp as omlp
+    out, o = [], 0
+    for shp in omlp.shapes(F, H, C):
+        k = int(np.prod(shp))
+        out.append(np.asarray(params[o:o + k], dtype=np.float64).reshape(shp))
+        o += k
+    assert o == len(params)
+    return out
+
+
+def test_host_inference_matches_oracle_network(bm, dg):
+    """bm_query_select (the host-side fp32 forward pass that routes single
+    queries) against argmin of oracle/mlp.py's fp64 forward on the features
+    bm_query_features reports, standardised in fp32 as the library does.
+    Where the oracle's two smallest predictions are within 1e-4 (fp32
+    rounding may order them either way) the pick must be one of those."""
+    from oracle import mlp as omlp
+    from paper_1402_4073_gb300 import selector
+    r_bits = 1 << 20
+    n_bm = 300
+    d = dg.pool_densities(dg.STREAM_TESTS + 14100, n_bm, 1e-5, 3e-2)
+    words = dg.bernoulli(dg.STREAM_TESTS + 14101, r_bits, d)
+    flat, offs = dg.positions(words, r_bits)
+    queries = dg.sparse_queries(400, pool=n_bm, nmax=300, stream=dg.STREAM_TESTS + 14102)
+    # a random network (no training needed to pin the inference), scaled so
+    # that the candidates' predictions differ
+    rng = np.random.default_rng(14103)
+    params = rng.normal(0.0, 0.4, bm.mlp_param_count()).astype(np.float32)
+    mean = rng.normal(0.0, 1.0, bm.SELECTOR_FEATURES).astype(np.float32)
+    std = rng.uniform(0.5, 2.0, bm.SELECTOR_FEATURES).astype(np.float32)
+    P = _unpack(params)
+    with bm.Pool(r_bits, n_bm) as pool:
+        pool.put_dense(words)
+        pool.put_positions(flat, offs)
+        bm.set_selector(pool, params, mean, std)
+        feats = np.stack([bm.query_features(pool, q) for q in queries]).astype(np.float32)
+        x = (feats - mean) / std  # fp32, as the library standardises
+        y, _ = omlp.forward(P, x.astype(np.float64))
+        picks = selector.installed_choices(pool, queries)
+    order = np.argsort(y, axis=1)
+    top, second = order[:, 0], order[:, 1]
+    margin = y[np.arange(len(y)), second] - y[np.arange(len(y)), top]
+    clear = margin > 1e-4
+    assert clear.sum() > 0.9 * len(queries)
+    assert np.array_equal(picks[clear], top[clear]), np.nonzero(picks[clear] != top[clear])
+    assert np.all((picks[~clear] == top[~clear]) | (picks[~clear] == second[~clear]))
+    # more than one candidate is picked, so the comparison sees the outputs differ
+    assert len(set(picks.tolist())) >= 2

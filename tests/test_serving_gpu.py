@@ -190,3 +190,40 @@ def test_run_length_requests(bm, oracle_lib, dg):
             with pytest.raises(bm.BMError) as e:
                 srv.submit(dg.Query(np.array([0, 32], dtype=np.uint32), 0, theta=1), path=bm.PATH_RLE)
             assert e.value.code == bm.BM_ERANGE
+
+
+def test_overload_sheds_by_latency_objective(bm, oracle_lib, dg):
+    """A burst far beyond what the GPU finishes within the objective: with
+    slo_us set, batches are sized to the oldest request's remaining time and
+    requests that cannot finish in time are dropped as expired, so the
+    admitted ones complete near the objective (bounded here by 3x, the
+    scheduler's estimates start from defaults) with the oracle's answers;
+    without it every request runs and the burst's tail waits far longer."""
+    from paper_1402_4073_gb300.serve import Server, summarize
+    r_bits = 1 << 22
+    d = dg.pool_densities(dg.STREAM_TESTS + 15200, 300, 1e-4, 0.5)
+    words = dg.bernoulli(dg.STREAM_TESTS + 15201, r_bits, d)
+    queries = dg.serving_queries(3000, 1e9, pool=300, nmax=300, stream=dg.STREAM_TESTS + 15202)
+    arrivals = [0.0] * len(queries)
+    slo = 3000
+    with bm.Pool(r_bits, 300) as pool:
+        pool.put_dense(words)
+        with Server(pool, mem_budget=_slots(pool, 1024), max_batch=1024, max_inflight=2,
+                    slo_us=slo) as srv:
+            srv.replay(queries[:200], arrivals[:200])  # warm-up: graphs, estimates
+            res = srv.replay(queries, arrivals)
+        s = summarize(res, 0.0, slo)
+        print("objective:", s)
+        assert s["errors"] == 0 and s["refused"] == 0
+        assert s["expired"] > 0 and s["completed"] > 0
+        assert s["completed"] + s["expired"] == len(queries)
+        assert s["p99_us"] <= 3 * slo
+        done = np.nonzero(res["status"] == 0)[0]
+        for i in done[:: max(1, len(done) // 40)]:
+            assert int(res["cards"][i]) == oracle_lib.query(words, queries[i], r_bits)[1]
+        with Server(pool, mem_budget=_slots(pool, 1024), max_batch=1024, max_inflight=2) as srv:
+            res2 = srv.replay(queries, arrivals)
+        s2 = summarize(res2, 0.0, slo)
+        print("no objective:", s2)
+        assert s2["completed"] == len(queries)
+        assert s2["p99_us"] > s["p99_us"]
