@@ -724,7 +724,7 @@ def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds:
     pool.put_dense(words)
     del words
     tune = pool.autotune()
-    out = []
+    out, results, slo = [], [], 0
     slot = (pool.words * 8 + 255) // 256 * 256
     # two batches of up to 2048 in flight: under overload, larger batches share each slab
     # of the pool among more queries (saturation 28.5k q/s at 512, 31.2k at 1024, 33.1k
@@ -742,14 +742,38 @@ def bench_serving(bm, datagen, rates=(1000, 5000, 10000, 20000, 50000), seconds:
             summ = summarize(res, float(rate))
             summ["requests"] = n
             out.append(summ)
+            if k == 0:
+                # the latency objective: ten times the p99 at the lowest offered rate
+                slo = int(10 * summ["p99_us"])
+            results.append(res)
         st = srv.stats()
+    for summ, res in zip(out, results):
+        summ.update({k2: v for k2, v in summarize(res, summ["offered_qps"], slo).items()
+                     if k2 in ("slo_us", "within_slo", "goodput_qps")})
+    # the same arrivals with load shedding by the objective (overloaded rates)
+    shed = []
+    with Server(pool, mem_budget=4096 * slot, max_batch=2048, max_inflight=2, slo_us=slo) as srv:
+        srv.replay(warm, [q.arrival_s for q in warm])
+        for k, rate in enumerate(rates):
+            if rate < 20000:
+                continue
+            n = int(min(40000, max(300 if small else 500, rate * seconds)))
+            qs = datagen.serving_queries(n, float(rate), pool=nbm, nmax=min(4096, nbm),
+                                         stream=datagen.STREAM_SERVING + ((10 + k) << 32))
+            res = srv.replay(qs, [q.arrival_s for q in qs])
+            summ = summarize(res, float(rate), slo)
+            summ["requests"] = n
+            shed.append(summ)
     pool.status()
     pool.close()
     return {"workload": f"serving: {nbm} x 2^22 pool (densities log-uniform [1e-5,0.5]), Poisson "
                         f"arrivals, N log-uniform [2,{min(4096, nbm)}], theta uniform [1,N]",
             "admission": "4096 result slots (2 GiB); max batch 2048; 2 batches in flight",
             "mean_batch": round(st["batched_queries"] / max(1, st["batches"]), 1),
-            "autotune": tune, "rates": out}
+            "autotune": tune, "rates": out,
+            "slo": f"{slo} us = 10 x p99 at the lowest offered rate; goodput = requests "
+                   "completed within it per second",
+            "rates_with_shedding": shed}
 
 
 def oracle_threads() -> int:
