@@ -503,7 +503,8 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
                 feats.emplace_back(kFeatures);
                 query_features(p, qi.ids, qi.n, truth[i], feats.back().data());
             } else {
-                cand[i] = with_rle(p, qi.ids, qi.n, rule_choice(p, qi.ids, qi.n));
+                cand[i] = with_rle(p, qi.ids, qi.n, rule_choice(p, qi.ids, qi.n),
+                                   kBatchDenseSpeedup);
             }
         } else {
             cand[i] = Candidate{qi.path, qi.path == BM_PATH_SPARSE ? p->sparse_cfg.tile_rows : 0u};
@@ -524,7 +525,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
             }
             if (c.path == BM_PATH_SPARSE && !lists) c = kCandidateTable[0];
             if (c.path == BM_PATH_DENSE && !dense) c = Candidate{BM_PATH_SPARSE, p->sparse_cfg.tile_rows};
-            cand[i] = with_rle(p, q[i].ids, q[i].n, c);
+            cand[i] = with_rle(p, q[i].ids, q[i].n, c, kBatchDenseSpeedup);
         }
     }
     std::vector<Pred> preds(nq);

@@ -101,7 +101,8 @@ Candidate select_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
 constexpr double kDenseUsPerMB = 0.145, kDenseFixedUs = 5.0;
 constexpr double kRleUsPerMB = 1.6, kRleRoundUs = 6.0;
 
-Candidate with_rle(const bm_pool* p, const uint32_t* ids, uint32_t n, Candidate c) {
+Candidate with_rle(const bm_pool* p, const uint32_t* ids, uint32_t n, Candidate c,
+                   double dense_speedup) {
     if (c.path != BM_PATH_DENSE || !all_have(p->rle_present, ids, n)) return c;
     uint64_t words = 0;  // runs and literal words, 8 bytes each
     for (uint32_t k = 0; k < n; ++k) words += p->rle_runs[ids[k]] + p->rle_lits[ids[k]];
@@ -109,7 +110,8 @@ Candidate with_rle(const bm_pool* p, const uint32_t* ids, uint32_t n, Candidate 
     const double rle_mb = (8.0 * (double)words + 4.0 * (double)n * tiles) / 1e6;
     const double dense_mb = (double)n * (double)p->r_bits / 8.0 / 1e6;
     const double rounds = std::ceil(tiles / (4.0 * (double)std::max(1, p->sm_count)));
-    if (kRleRoundUs * rounds + kRleUsPerMB * rle_mb < kDenseFixedUs + kDenseUsPerMB * dense_mb)
+    if (kRleRoundUs * rounds + kRleUsPerMB * rle_mb <
+        (kDenseFixedUs + kDenseUsPerMB * dense_mb) / dense_speedup)
         return Candidate{BM_PATH_RLE, 0};
     return c;
 }

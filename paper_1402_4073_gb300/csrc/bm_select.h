@@ -39,7 +39,14 @@ Candidate select_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
 // The run-length path in place of a dense choice c when every input has a
 // run-length form and the estimated time of reading its runs, literal words
 // and tile summaries is below that of reading the dense words; else c.
-Candidate with_rle(const bm_pool* p, const uint32_t* ids, uint32_t n, Candidate c);
+// dense_speedup divides the dense estimate: a query left in a batch's dense
+// kernel shares the pool's slabs through L2 with the other queries
+// (kBatchDenseSpeedup), while a run-length query runs as a launch of its own.
+Candidate with_rle(const bm_pool* p, const uint32_t* ids, uint32_t n, Candidate c,
+                   double dense_speedup = 1.0);
+// Queries per second of the batch's dense kernel over one launch per query
+// on the mixed batch workload (measured on GB300: 38.0k vs 15.2k).
+constexpr double kBatchDenseSpeedup = 2.5;
 
 // A single query's choice: select_candidate, then with_rle.
 Candidate single_query_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
