@@ -9,7 +9,8 @@ suboptimality, (t - t_best) / t_best (App. C).  Here a small network
 from the query's features; the smallest prediction wins.
 
 * ``collect``: time every candidate on every query with the library's own
-  kernels (CUDA events, median of repeats) and read each query's features.
+  kernels (CUDA events around calls queued back to back) and read each
+  query's features.
 * ``train``: fit the network to the log times on the GPU with the library's
   forward, backward and Adam kernels.
 * ``time_lost``: sum(t_chosen - t_best) / sum(t_best) over a query set, the
@@ -25,8 +26,8 @@ import numpy as np
 import torch
 
 from . import (CANDIDATES, PATH_AUTO, PATH_DENSE, PATH_SPARSE, SELECTOR_CANDIDATES,
-               SELECTOR_FEATURES, SELECTOR_HIDDEN, Pool, mlp_adam, mlp_backward, mlp_forward,
-               mlp_param_count, query_features, query_run, query_select, set_selector)
+               SELECTOR_FEATURES, SELECTOR_HIDDEN, Pool, PreparedQuery, mlp_adam, mlp_backward,
+               mlp_forward, mlp_param_count, query_features, query_select, set_selector)
 
 
 @dataclass
@@ -38,29 +39,36 @@ class Model:
 
 
 def collect(pool: Pool, queries, reps: int = 3, stream=None):
-    """(features [n, 5], times_us [n, 4]) for every query and candidate."""
+    """(features [n, 5], times_us [n, 4]) for every query and candidate: the
+    device time per call, `reps` calls queued back to back behind a short
+    sleep kernel (so that the host's own per-call time, the same for every
+    candidate, is not measured), mean per call."""
     stream = stream or torch.cuda.current_stream()
     info = pool.info()
     feats = np.stack([query_features(pool, q) for q in queries]).astype(np.float32)
     times = np.full((len(queries), SELECTOR_CANDIDATES), np.nan, dtype=np.float64)
     out = pool.empty_words()
     card = torch.zeros(1, dtype=torch.int64, device=out.device)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     saved = pool.configs()["sparse"]
+    sleep = getattr(torch.cuda, "_sleep", None)
     for c, (path, tile) in enumerate(CANDIDATES):
         if path == PATH_SPARSE:
             if info["lists_loaded"] == 0:
                 continue
             pool.set_sparse_config(tile, saved["threads"], saved["ctas_per_sm"], saved["unroll"])
         for i, q in enumerate(queries):
-            query_run(pool, q, out, card, path=path, stream=stream)  # warm-up
-            for r in range(reps):
-                ev[2 * r].record(stream)
-                query_run(pool, q, out, card, path=path, stream=stream)
-                ev[2 * r + 1].record(stream)
+            pq = PreparedQuery(pool, q, out, path)
+            pq.run(card, stream)  # warm-up
+            with torch.cuda.stream(stream):
+                if sleep is not None:
+                    sleep(100_000 * reps)  # about 50 us per call: the host queues the calls
+                e0.record(stream)
+                for _ in range(reps):
+                    pq.run(card, stream)
+                e1.record(stream)
             stream.synchronize()
-            times[i, c] = np.median([ev[2 * r].elapsed_time(ev[2 * r + 1]) * 1e3
-                                     for r in range(reps)])
+            times[i, c] = e0.elapsed_time(e1) * 1e3 / reps
     pool.set_sparse_config(**saved)
     return feats, times
 
