@@ -164,6 +164,35 @@ __device__ __forceinline__ uint64_t eval_offset(const uint32_t (&P)[2][K], const
     return (uint64_t)eval_pred<K>(P[0], q, tab) | ((uint64_t)eval_pred<K>(P[1], q, tab) << 32);
 }
 
+// The pruning of RBMrg over a whole tile (Sec. 4.1): every row's count lies
+// in [lo, hi], lo = the inputs that are one clean-1 run over the tile (k in
+// the paper), hi = lo + the inputs left to decode.  When f takes one value
+// over [lo, hi] (for a threshold T: T - k <= 0, or T - k beyond the inputs
+// left), that value is the tile's output and nothing needs decoding.
+// Returns it, or -1.  tab: f over 0..n (mode 2).
+__device__ __forceinline__ int constant_over(const Pred& p, const uint32_t* tab, uint32_t lo,
+                                             uint32_t hi) {
+    if (p.mode == 0) return (int)p.v0;
+    if (p.mode == 1) {
+        uint32_t v = p.v0;
+#pragma unroll
+        for (int i = 0; i < kMaxTransitions; ++i) {
+            if ((uint32_t)i >= p.ntrans) break;
+            if (p.trans[i] <= lo) v ^= 1u;
+            else if (p.trans[i] <= hi) return -1;
+        }
+        return (int)v;
+    }
+    const uint32_t v = (tab[lo >> 5] >> (lo & 31u)) & 1u;
+    for (uint32_t w = lo >> 5; w <= (hi >> 5); ++w) {
+        uint32_t m = ~0u;
+        if (w == (lo >> 5)) m &= ~0u << (lo & 31u);
+        if (w == (hi >> 5) && (hi & 31u) != 31u) m &= (2u << (hi & 31u)) - 1u;
+        if ((tab[w] ^ (v ? ~0u : 0u)) & m) return -1;
+    }
+    return (int)v;
+}
+
 template <int K>
 __global__ void __launch_bounds__(kRleThreads, K <= 9 ? 4 : (K <= 13 ? 3 : 2))
     rle_kernel(RleArgs a, const __grid_constant__ LaunchExtra x) {
@@ -212,6 +241,7 @@ __global__ void __launch_bounds__(kRleThreads, K <= 9 ? 4 : (K <= 13 ? 3 : 2))
         const uint32_t w1 = (uint32_t)min((uint64_t)w0 + kRleTileWords, a.words);
         uint32_t P[2][K];
         zero_planes<K, 2>(P);
+        int konst = -1;  // the tile's output when it needs no decoding
         if (tid == 0) {
             s_c1 = 0u;
             cov[kRleThreads] = 0;
@@ -241,7 +271,9 @@ __global__ void __launch_bounds__(kRleThreads, K <= 9 ? 4 : (K <= 13 ? 3 : 2))
             __syncthreads();
             if (one_chunk) load_sums(m, tile + gridDim.x, sum_next);  // in flight while decoding
             const uint32_t nd = s_nd;
+            if (one_chunk) konst = constant_over(a.pred, tab, s_c1, s_c1 + nd);
             __syncthreads();  // every thread has nd before the next chunk resets it
+            if (konst >= 0) break;  // the whole tile is one value: no decoding
             for (uint32_t g0 = 0; g0 < nd; g0 += kRleGroup) {
                 const uint32_t gn = min(kRleGroup, nd - g0);
                 // half-warp h of the CTA decodes entry h of the group into stage row h
@@ -286,6 +318,17 @@ __global__ void __launch_bounds__(kRleThreads, K <= 9 ? 4 : (K <= 13 ? 3 : 2))
                 }
                 __syncthreads();
             }
+        }
+        if (konst >= 0) {
+            const uint64_t col = (uint64_t)w0 + tid;
+            if (col < a.words) {
+                uint64_t word = konst ? ~0ull : 0ull;
+                if (col == a.words - 1 && (a.r_bits & 63u)) word &= (1ull << (a.r_bits & 63u)) - 1ull;
+                a.out[col] = word;
+                card += (unsigned long long)__popcll(word);
+            }
+            __syncthreads();  // s_c1, s_nd are reused by the next tile
+            continue;
         }
         __syncthreads();  // c1 and the coverage differences are final
         // coverage of this thread's column: inclusive prefix sum of cov

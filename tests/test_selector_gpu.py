@@ -89,18 +89,24 @@ def test_host_inference_matches_oracle_network(bm, dg):
     words = dg.bernoulli(dg.STREAM_TESTS + 14101, r_bits, d)
     flat, offs = dg.positions(words, r_bits)
     queries = dg.sparse_queries(400, pool=n_bm, nmax=300, stream=dg.STREAM_TESTS + 14102)
-    # a random network (no training needed to pin the inference), scaled so
-    # that the candidates' predictions differ
+    # a random network (no training needed to pin the inference): weights
+    # N(0, 1/fan_in), zero biases, features standardised by their own mean
+    # and deviation as training does, so that the picks differ across queries
     rng = np.random.default_rng(14103)
-    params = rng.normal(0.0, 0.4, bm.mlp_param_count()).astype(np.float32)
-    mean = rng.normal(0.0, 1.0, bm.SELECTOR_FEATURES).astype(np.float32)
-    std = rng.uniform(0.5, 2.0, bm.SELECTOR_FEATURES).astype(np.float32)
+    parts = []
+    for shp in omlp.shapes():
+        parts.append(rng.normal(0.0, 1.0 / np.sqrt(shp[0]), shp).ravel() if len(shp) == 2
+                     else np.zeros(shp))
+    params = np.concatenate(parts).astype(np.float32)
     P = _unpack(params)
     with bm.Pool(r_bits, n_bm) as pool:
         pool.put_dense(words)
         pool.put_positions(flat, offs)
-        bm.set_selector(pool, params, mean, std)
         feats = np.stack([bm.query_features(pool, q) for q in queries]).astype(np.float32)
+        mean = feats.mean(axis=0).astype(np.float32)
+        std = feats.std(axis=0).astype(np.float32)
+        std[std < 1e-6] = 1.0
+        bm.set_selector(pool, params, mean, std)
         x = (feats - mean) / std  # fp32, as the library standardises
         y, _ = omlp.forward(P, x.astype(np.float64))
         picks = selector.installed_choices(pool, queries)
