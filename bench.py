@@ -235,6 +235,7 @@ def bench_batched(bm, datagen, passes: int = 2, small: bool = False, config: str
     same = bool(torch.equal(cards_plain, cards_batch))
     pool.status()
     logical = sum(query_bytes(q.n, r_bits) for q in queries)
+    l2_gbps = l2_copy_peak()
     # integer roofline: ~2 three-input logic ops per 32-bit input word (one
     # full adder per input in the sideways-sum tree, Sec. 4.3), against
     # SMs x 64 int32 lanes x the maximum SM clock
@@ -253,8 +254,36 @@ def bench_batched(bm, datagen, passes: int = 2, small: bool = False, config: str
             "speedup": round(t_plain / t_batch, 3),
             "plain_logical_GBps": round(logical / t_plain / 1e9, 1),
             "batched_logical_GBps": round(logical / t_batch / 1e9, 1),
+            "l2_roofline": {"bound": "l2", "achieved_GBps": round(logical / t_batch / 1e9, 1),
+                            "peak_GBps": round(l2_gbps, 1),
+                            "frac": round(logical / t_batch / 1e9 / l2_gbps, 4),
+                            "peak_source": "measured here: device copy between two 24 MiB "
+                                           "buffers (L2-resident), read + write bytes, best of 20"},
             "cardinalities_equal": same, "timing": f"best of {passes} passes, CUDA events",
             "autotune": tune}
+
+
+def l2_copy_peak() -> float:
+    """GB/s of a device copy from one 24 MiB buffer to another (48 MiB in all,
+    L2-resident; read + write bytes), best of 20: the bandwidth the batch
+    kernel, whose inputs are served from L2 after the first query of a slab,
+    is held against."""
+    import torch
+    a = torch.empty(6 << 20, dtype=torch.int32, device="cuda").fill_(1)
+    b = torch.empty_like(a)
+    stream = torch.cuda.current_stream()
+    best = 0.0
+    for _ in range(3):
+        b.copy_(a)
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            b.copy_(a)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, 10 * 2 * a.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
 
 
 def bench_selector(bm, datagen, n_train: int = 600, small: bool = False):
@@ -366,12 +395,21 @@ def bench_sparse(bm, datagen, reps: int = 20, small: bool = False, config: str =
         us = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(reps)) * 1e3
         b = int(lens[ids].sum())
         alg = 4 * b + r_bits // 8
-        cold, hot = call_times(lambda: pq.run(card), reps, flush)
+        # device time per call on each tile size the selector can pick
+        tuned = pool.configs()["sparse"]
+        by_tile = {}
+        for tile in (16384, 32768, 65536):
+            pool.set_sparse_config(tile, tuned["threads"], tuned["ctas_per_sm"], tuned["unroll"])
+            by_tile[tile] = call_times(lambda: pq.run(card), reps, flush)
+        pool.set_sparse_config(**tuned)
+        best = min(by_tile, key=lambda t: by_tile[t][0])
+        cold, hot = by_tile[best]
         rows.append({"N": n, "positions": b, "us_per_query": round(us, 1),
                      "achieved_GBps": round(alg / us / 1e3, 1),
                      "frac": round(alg / us / 1e3 / peak, 4),
-                     "cold_us": round(cold, 2), "cold_frac": round(alg / cold / 1e3 / peak, 4),
-                     "hot_us": round(hot, 2)})
+                     "tile_rows": best, "cold_us": round(cold, 2),
+                     "cold_frac": round(alg / cold / 1e3 / peak, 4), "hot_us": round(hot, 2),
+                     "cold_us_by_tile": {str(t): round(v[0], 2) for t, v in by_tile.items()}})
     pool.status()
     pool.close()
     cos = bench_cosparse(bm, datagen, r_bits, nbm, reps, peak, config)
@@ -379,8 +417,9 @@ def bench_sparse(bm, datagen, reps: int = 20, small: bool = False, config: str =
                         "(densities log-uniform [1e-5,1e-2], position lists), theta=min(N,8)",
             "kernel": "ScanCount (scancount_kernel)", "bytes": "4 * positions + r/8 per query",
             "peak": peak, "peak_source": f"hbm_gbs of {peak_src}",
-            "timing": f"us_per_query: median of {reps} launches, CUDA events around each "
-                      "bm_query_run (host time inside); cold/hot: see the small part",
+            "timing": f"us_per_query / frac: median of {reps} launches of the tuned tile, CUDA "
+                      "events around each bm_query_run (host time inside); cold/hot (as in the "
+                      "small part) on the best of the selector's three tile sizes",
             "queries": rows, "autotune": tune, "co_sparse": cos}
 
 
