@@ -173,6 +173,143 @@ __device__ __forceinline__ void count_tile(uint32_t* cnt, uint32_t* scratch, uin
     }
 }
 
+// 16-byte asynchronous copy global -> shared (cp.async, L2 only) and its
+// group bookkeeping.  A thread's copies are complete for that thread after
+// the matching wait; here every lane reads back only what it copied itself.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// count_tile with the loads staged through shared memory: a warp's pieces
+// are read in windows of W pieces (32 vectors each), two windows in flight,
+// each vector copied by cp.async into `stage` (2 W 32 vectors per warp) by
+// the lane that counts it, so the loads in flight hold no registers.  A lane
+// whose vector lies past the stream issues no copy and counts nothing.
+// Arguments, layout and results as count_tile.
+template <int BITS, int W, typename IdOf>
+__device__ __forceinline__ void count_tile_staged(uint32_t* cnt, uint32_t* scratch, uint4* stage,
+                                                  uint32_t* s_next, IdOf id_of, uint32_t n,
+                                                  const uint4* vpos, const uint64_t* list_begin,
+                                                  const uint32_t* tile_index,
+                                                  uint32_t tiles_per_list, uint64_t t0,
+                                                  uint64_t t1, uint32_t lo, uint32_t nrows,
+                                                  uint32_t cnt_rows, uint32_t d_fill) {
+    constexpr uint32_t kFull = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t le = (2u << lane) - 1u, lt = (1u << lane) - 1u;
+    const uint32_t spare = cnt_rows + lane * (32 / BITS);  // this lane's spare counter word
+    const uint32_t ngroups = (n + 31) / 32;
+    uint32_t* ws = scratch + warp * kScanWarpWords;  // [0,32): first vector | zeros bit, [32,64): offset
+    uint4* st = stage + (size_t)warp * (2 * W * 32) + lane;
+    if (threadIdx.x == 0) *s_next = nw;
+    if (d_fill) {  // the rows' counters (those evaluated) start at d_fill
+        const uint32_t fill = BITS == 8 ? d_fill * 0x01010101u : d_fill * 0x00010001u;
+        const uint32_t words = (nrows + 31) / 32 * BITS;  // BITS words per 32 rows
+        for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) cnt[i] = fill;
+    }
+    __syncthreads();
+    auto bounds = [&](uint32_t g, uint32_t& vs, uint32_t& nv) {
+        vs = 0u;
+        nv = 0u;
+        const uint32_t j = g * 32 + lane;
+        if (g < ngroups && j < n) {
+            const uint32_t id = id_of(j);
+            const uint32_t* idx = tile_index + (uint64_t)id * (tiles_per_list + 1);
+            const uint32_t b = __ldg(idx + t0), en = __ldg(idx + t1);
+            const uint64_t begin = __ldg(list_begin + id);
+            const uint64_t base = begin & ~kListComplement;
+            vs = (uint32_t)((base + b) >> 2);
+            nv = b < en ? (uint32_t)((base + en + 3) >> 2) - vs : 0u;
+            vs |= (uint32_t)(begin >> 32) & 0x80000000u;  // bit 31: a list of zeros
+        }
+    };
+    uint32_t team = 1;
+    while (ngroups && team * 2 * ngroups <= nw) team *= 2;
+    const uint32_t units = ngroups * team;
+    uint32_t u = warp, vs, nv;
+    bounds(u / team, vs, nv);
+    while (u < units) {
+        uint32_t un = 0;
+        if (lane == 0) un = atomicAdd(s_next, 1u);
+        un = __shfl_sync(kFull, un, 0);
+        uint32_t vs_n, nv_n;
+        bounds(un < units ? un / team : ngroups, vs_n, nv_n);  // in flight while this unit is counted
+        uint32_t inc = nv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= (uint32_t)o) inc += y;
+        }
+        const uint32_t start = inc - nv;
+        const uint32_t total = __shfl_sync(kFull, inc, 31);
+        const uint32_t ne = __ballot_sync(kFull, nv != 0u);
+        if (nv) {
+            const uint32_t rk = __popc(ne & lt);
+            ws[rk] = vs;
+            ws[32 + rk] = start;
+        }
+        __syncwarp();
+        const uint32_t pieces = (total + 31) / 32;
+        const uint32_t member = u % team;
+        const uint32_t mine = pieces > member ? (pieces - member + team - 1) / team : 0u;
+        // copy window k0 (pieces k0 .. k0 + W - 1 of this warp) into buffer buf;
+        // valid / subs: per piece, the lane copied a vector / of a list of zeros
+        auto issue = [&](uint32_t k0, uint32_t buf, uint32_t& valid, uint32_t& subs) {
+            valid = 0u;
+            subs = 0u;
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                const uint32_t q = member + (k0 + i) * team;
+                if (k0 + i < mine) {  // uniform across the warp
+                    const uint32_t before = __popc(__ballot_sync(kFull, nv != 0u && start < q * 32));
+                    const uint32_t inside = __reduce_or_sync(
+                        kFull, (nv != 0u && (start >> 5) == q) ? (1u << (start & 31)) : 0u);
+                    const uint32_t r = before + __popc(inside & le) - 1u;
+                    const uint32_t v = q * 32 + lane;
+                    if (v < total) {
+                        const uint32_t first = ws[r];
+                        cp_async16(st + (buf * W + i) * 32,
+                                   vpos + (first & 0x7FFFFFFFu) + (v - ws[32 + r]));
+                        valid |= 1u << i;
+                        subs |= (first >> 31) << i;
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+        auto consume = [&](uint32_t buf, uint32_t valid, uint32_t subs) {
+#pragma unroll
+            for (int i = 0; i < W; ++i)
+                if ((valid >> i) & 1u)
+                    count_vec<BITS>(cnt, st[(buf * W + i) * 32], lo, nrows, spare, (subs >> i) & 1u);
+        };
+        uint32_t va, sa, vb, sb;
+        issue(0, 0, va, sa);
+        for (uint32_t k0 = 0; k0 < mine; k0 += 2 * W) {
+            issue(k0 + W, 1, vb, sb);  // an empty window past the end
+            cp_async_wait<1>();
+            consume(0, va, sa);
+            if (k0 + W >= mine) break;
+            issue(k0 + 2 * W, 0, va, sa);
+            cp_async_wait<1>();
+            consume(1, vb, sb);
+        }
+        cp_async_wait<0>();
+        __syncwarp();  // the group's slices are read before the next unit writes them
+        u = un;
+        vs = vs_n;
+        nv = nv_n;
+    }
+}
+
 // One 32-bit output lane from 32 counters (words cw[0 .. kWords), 16-byte
 // aligned), which are cleared as they are read, ready for the next tile.
 // The words are read 16 bytes at a time; a chunk whose counters are all zero
