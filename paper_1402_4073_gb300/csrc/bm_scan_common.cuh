@@ -188,20 +188,23 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// count_tile with the loads staged through shared memory: a warp's pieces
-// are read in windows of W pieces (32 vectors each), two windows in flight,
-// each vector copied by cp.async into `stage` (2 W 32 vectors per warp) by
-// the lane that counts it, so the loads in flight hold no registers.  A lane
-// whose vector lies past the stream issues no copy and counts nothing.
-// Arguments, layout and results as count_tile.
+// count_tile with the loads staged through shared memory and pipelined across
+// the warp's units: vectors are copied by cp.async into `stage` (two windows
+// of W pieces of 32 vectors per warp), each by the lane that will count it,
+// so loads in flight hold no registers; a window is filled from as many of
+// the warp's units as it takes, so the next unit's first loads are in flight
+// while the current unit's last pieces are counted.  The slice bounds of the
+// next unit are loaded ahead (one unit: a warp holds at most two, so units
+// still balance the warps' work).  Arguments, layout and results as
+// count_tile.
 template <int BITS, int W, typename IdOf>
-__device__ __forceinline__ void count_tile_staged(uint32_t* cnt, uint32_t* scratch, uint4* stage,
-                                                  uint32_t* s_next, IdOf id_of, uint32_t n,
-                                                  const uint4* vpos, const uint64_t* list_begin,
-                                                  const uint32_t* tile_index,
-                                                  uint32_t tiles_per_list, uint64_t t0,
-                                                  uint64_t t1, uint32_t lo, uint32_t nrows,
-                                                  uint32_t cnt_rows, uint32_t d_fill) {
+__device__ __forceinline__ void count_tile_pipe(uint32_t* cnt, uint32_t* scratch, uint4* stage,
+                                                uint32_t* s_next, IdOf id_of, uint32_t n,
+                                                const uint4* vpos, const uint64_t* list_begin,
+                                                const uint32_t* tile_index,
+                                                uint32_t tiles_per_list, uint64_t t0, uint64_t t1,
+                                                uint32_t lo, uint32_t nrows, uint32_t cnt_rows,
+                                                uint32_t d_fill) {
     constexpr uint32_t kFull = 0xFFFFFFFFu;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t le = (2u << lane) - 1u, lt = (1u << lane) - 1u;
@@ -234,22 +237,27 @@ __device__ __forceinline__ void count_tile_staged(uint32_t* cnt, uint32_t* scrat
     uint32_t team = 1;
     while (ngroups && team * 2 * ngroups <= nw) team *= 2;
     const uint32_t units = ngroups * team;
-    uint32_t u = warp, vs, nv;
-    bounds(u / team, vs, nv);
-    while (u < units) {
-        uint32_t un = 0;
-        if (lane == 0) un = atomicAdd(s_next, 1u);
-        un = __shfl_sync(kFull, un, 0);
-        uint32_t vs_n, nv_n;
-        bounds(un < units ? un / team : ngroups, vs_n, nv_n);  // in flight while this unit is counted
+    auto take = [&]() {  // the warp's next unit (uniform)
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(s_next, 1u);
+        return __shfl_sync(kFull, t, 0);
+    };
+    // the unit being issued (u, its slice table in ws) and the next one
+    uint32_t u = warp, ua = take();
+    uint32_t vs, nv, vsa, nva;
+    bounds(u < units ? u / team : ngroups, vs, nv);
+    bounds(ua < units ? ua / team : ngroups, vsa, nva);
+    uint32_t start = 0, total = 0, mine = 0, member = 0, k = 0;
+    auto setup = [&]() {  // lay unit u's slices end to end in ws
+        __syncwarp();     // the previous unit's lookups are done with ws
         uint32_t inc = nv;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(kFull, inc, o);
             if (lane >= (uint32_t)o) inc += y;
         }
-        const uint32_t start = inc - nv;
-        const uint32_t total = __shfl_sync(kFull, inc, 31);
+        start = inc - nv;
+        total = __shfl_sync(kFull, inc, 31);
         const uint32_t ne = __ballot_sync(kFull, nv != 0u);
         if (nv) {
             const uint32_t rk = __popc(ne & lt);
@@ -258,56 +266,67 @@ __device__ __forceinline__ void count_tile_staged(uint32_t* cnt, uint32_t* scrat
         }
         __syncwarp();
         const uint32_t pieces = (total + 31) / 32;
-        const uint32_t member = u % team;
-        const uint32_t mine = pieces > member ? (pieces - member + team - 1) / team : 0u;
-        // copy window k0 (pieces k0 .. k0 + W - 1 of this warp) into buffer buf;
-        // valid / subs: per piece, the lane copied a vector / of a list of zeros
-        auto issue = [&](uint32_t k0, uint32_t buf, uint32_t& valid, uint32_t& subs) {
-            valid = 0u;
-            subs = 0u;
+        member = u % team;
+        mine = pieces > member ? (pieces - member + team - 1) / team : 0u;
+        k = 0;
+    };
+    auto advance = [&]() {  // move to the next unit, taking one more ahead
+        u = ua;
+        vs = vsa;
+        nv = nva;
+        ua = take();
+        bounds(ua < units ? ua / team : ngroups, vsa, nva);
+        if (u < units) setup();
+    };
+    if (u < units) setup();
+    // fill window buffer buf with the warp's next W pieces, across units;
+    // returns whether any piece was issued (uniform)
+    auto issue = [&](uint32_t buf, uint32_t& valid, uint32_t& subs) {
+        valid = 0u;
+        subs = 0u;
+        bool any = false;
 #pragma unroll
-            for (int i = 0; i < W; ++i) {
-                const uint32_t q = member + (k0 + i) * team;
-                if (k0 + i < mine) {  // uniform across the warp
-                    const uint32_t before = __popc(__ballot_sync(kFull, nv != 0u && start < q * 32));
-                    const uint32_t inside = __reduce_or_sync(
-                        kFull, (nv != 0u && (start >> 5) == q) ? (1u << (start & 31)) : 0u);
-                    const uint32_t r = before + __popc(inside & le) - 1u;
-                    const uint32_t v = q * 32 + lane;
-                    if (v < total) {
-                        const uint32_t first = ws[r];
-                        cp_async16(st + (buf * W + i) * 32,
-                                   vpos + (first & 0x7FFFFFFFu) + (v - ws[32 + r]));
-                        valid |= 1u << i;
-                        subs |= (first >> 31) << i;
-                    }
+        for (int i = 0; i < W; ++i) {
+            while (u < units && k >= mine) advance();
+            if (u < units) {  // uniform across the warp
+                const uint32_t q = member + k * team;
+                const uint32_t before = __popc(__ballot_sync(kFull, nv != 0u && start < q * 32));
+                const uint32_t inside = __reduce_or_sync(
+                    kFull, (nv != 0u && (start >> 5) == q) ? (1u << (start & 31)) : 0u);
+                const uint32_t r = before + __popc(inside & le) - 1u;
+                const uint32_t v = q * 32 + lane;
+                if (v < total) {
+                    const uint32_t first = ws[r];
+                    cp_async16(st + (buf * W + i) * 32,
+                               vpos + (first & 0x7FFFFFFFu) + (v - ws[32 + r]));
+                    valid |= 1u << i;
+                    subs |= (first >> 31) << i;
                 }
+                ++k;
+                any = true;
             }
-            cp_async_commit();
-        };
-        auto consume = [&](uint32_t buf, uint32_t valid, uint32_t subs) {
-#pragma unroll
-            for (int i = 0; i < W; ++i)
-                if ((valid >> i) & 1u)
-                    count_vec<BITS>(cnt, st[(buf * W + i) * 32], lo, nrows, spare, (subs >> i) & 1u);
-        };
-        uint32_t va, sa, vb, sb;
-        issue(0, 0, va, sa);
-        for (uint32_t k0 = 0; k0 < mine; k0 += 2 * W) {
-            issue(k0 + W, 1, vb, sb);  // an empty window past the end
-            cp_async_wait<1>();
-            consume(0, va, sa);
-            if (k0 + W >= mine) break;
-            issue(k0 + 2 * W, 0, va, sa);
-            cp_async_wait<1>();
-            consume(1, vb, sb);
         }
-        cp_async_wait<0>();
-        __syncwarp();  // the group's slices are read before the next unit writes them
-        u = un;
-        vs = vs_n;
-        nv = nv_n;
+        cp_async_commit();
+        return any;
+    };
+    auto consume = [&](uint32_t buf, uint32_t valid, uint32_t subs) {
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+            if ((valid >> i) & 1u)
+                count_vec<BITS>(cnt, st[(buf * W + i) * 32], lo, nrows, spare, (subs >> i) & 1u);
+    };
+    uint32_t va, sa, vb, sb;
+    bool a_any = issue(0, va, sa);
+    while (a_any) {
+        const bool b_any = issue(1, vb, sb);
+        cp_async_wait<1>();
+        consume(0, va, sa);
+        if (!b_any) break;
+        a_any = issue(0, va, sa);
+        cp_async_wait<1>();
+        consume(1, vb, sb);
     }
+    cp_async_wait<0>();
 }
 
 // One 32-bit output lane from 32 counters (words cw[0 .. kWords), 16-byte

@@ -44,14 +44,8 @@ __device__ void build_truth(const Pred& pr, uint32_t n, uint32_t* tab, uint32_t 
 }
 
 // Two 512-thread CTAs per SM.  The loads of a warp's pieces go to shared
-// memory (count_tile_staged), two windows of W pieces in flight per warp.
-//
-// CTA b owns the contiguous rows of index tiles [T b / G, T (b + 1) / G)
-// (T = ceil(r / 8192) index tiles, G CTAs) and counts them in passes of
-// tile_rows rows (the last pass of a CTA may be shorter), so every CTA has
-// the same rows to within one index tile whatever r is, instead of whole
-// tiles dealt round-robin (3.37 tiles per CTA at r = 2^24 left most CTAs idle
-// during the last round).
+// memory (count_tile_pipe), two windows of W pieces in flight per warp,
+// continuing from one unit of lists to the next.
 template <int BITS, int W>  // counter width: 8 or 16; pieces per load window
 __global__ void __launch_bounds__(512, 2)
     scancount_kernel(SparseArgs a, const __grid_constant__ LaunchExtra x) {
@@ -68,18 +62,18 @@ __global__ void __launch_bounds__(512, 2)
     uint4* stage = reinterpret_cast<uint4*>(cnt + cnt_words + 32);  // past the spare words
     build_truth(a.pred, a.n, tab, tab_words);
 
-    const uint64_t nidx = a.tiles_per_list;
-    const uint64_t i0 = nidx * blockIdx.x / gridDim.x, i1 = nidx * (blockIdx.x + 1) / gridDim.x;
-    const uint32_t sub = a.tile_rows / kListTileRows;  // index entries per pass
+    const uint64_t ntiles = (a.r_bits + a.tile_rows - 1) / a.tile_rows;
+    const uint32_t sub = a.tile_rows / kListTileRows;  // index entries per tile
     unsigned long long card = 0;
-    // counters start at zero; evaluating a pass clears them for the next one
+    // counters start at zero; evaluating a tile clears them for the next one
     for (uint32_t i = threadIdx.x; i < cnt_words; i += blockDim.x) cnt[i] = 0u;
     __syncthreads();
-    for (uint64_t t0 = i0; t0 < i1; t0 += sub) {
-        const uint64_t t1 = min(t0 + sub, i1);
-        const uint64_t lo = t0 * kListTileRows;
-        const uint64_t hi = min(t1 * kListTileRows, a.r_bits);
-        count_tile_staged<BITS, W>(
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t lo = tile * a.tile_rows;
+        const uint64_t hi = min(lo + a.tile_rows, a.r_bits);
+        const uint64_t t0 = tile * sub;
+        const uint64_t t1 = (t0 + sub < a.tiles_per_list) ? t0 + sub : (uint64_t)a.tiles_per_list;
+        count_tile_pipe<BITS, W>(
             cnt, scratch, stage, &s_next,
             [&](uint32_t j) { return x.n_inline ? s_ids[j] : __ldg(a.ids + j); }, a.n,
             reinterpret_cast<const uint4*>(a.positions), a.list_begin, a.tile_index,
@@ -128,12 +122,13 @@ int launch_sparse(const SparseArgs& a, const LaunchExtra& x, const SparseConfig&
         if (smem > 48 * 1024)
             BM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem));
-        // one resident wave: each CTA owns an even share of the rows
+        // persistent: at most one resident wave
         int per_sm = 0;
         BM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
         if (per_sm < 1) return BM_EINVAL;
         const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::min(per_sm, std::max(1, cfg.ctas_per_sm));
-        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(b.tiles_per_list, cap));
+        const uint64_t ntiles = (b.r_bits + b.tile_rows - 1) / b.tile_rows;
+        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ntiles, cap));
         fn<<<grid, threads, smem, s>>>(b, x);
         BM_CUDA_TRY(cudaGetLastError());
         return BM_OK;
