@@ -498,10 +498,13 @@ int bm_server_stats(bm_server* server, bm_server_stats_t* out);
 /* Number of selector features and candidates (the network's in/outputs). */
 #define BM_SELECTOR_FEATURES 5u
 #define BM_SELECTOR_HIDDEN 64u
-#define BM_SELECTOR_CANDIDATES 4u
+#define BM_SELECTOR_CANDIDATES 5u
 /*
- * Candidate c runs: 0 = dense counter; 1, 2, 3 = ScanCount with tiles of
- * 16384, 32768, 65536 rows.
+ * Candidate c runs: 0 = dense counter in the pool's shape; 1, 2, 3 = ScanCount
+ * with tiles of 16384, 32768, 65536 rows; 4 = dense counter with one 64-bit
+ * word per thread (direct loads, twice the threads: for queries whose rows
+ * leave the pool's shape short of parallelism).  In a batch, candidates 0 and
+ * 4 both run in the batch's dense kernel.
  */
 
 /*
@@ -513,7 +516,7 @@ int bm_query_features(const bm_pool* pool, const bm_query* q, float* out);
 
 /*
  * Install a trained selector: params (host fp32, the layout of
- * bm_mlp_forward with F = 5, H = 64, C = 4) predicts each candidate's log
+ * bm_mlp_forward with F = 5, H = 64, C = 5) predicts each candidate's log
  * time from the standardised features (x - mean) / std.  Queries with
  * path BM_PATH_AUTO then run the candidate with the smallest prediction
  * among those whose inputs are loaded.  params = NULL removes it (the fixed
@@ -522,8 +525,10 @@ int bm_query_features(const bm_pool* pool, const bm_query* q, float* out);
 int bm_pool_set_selector(bm_pool* pool, const float* params, uint64_t nparams, const float* mean,
                          const float* stdev, uint32_t n_out);
 
-/* The path and sparse tile rows that BM_PATH_AUTO would pick for q as a
-   single query (bm_query_run). */
+/* The path that BM_PATH_AUTO would pick for q as a single query
+   (bm_query_run); *tile_rows (may be NULL) receives, for BM_PATH_SPARSE, the
+   tile rows; for BM_PATH_DENSE, 1 when the one-word-per-thread shape
+   (candidate 4) is picked, else 0; for BM_PATH_RLE, 0. */
 int bm_query_select(const bm_pool* pool, const bm_query* q, int32_t* path, uint32_t* tile_rows);
 
 /*

@@ -77,9 +77,11 @@ uint32_t complement_inputs(const bm_pool* p, const uint32_t* ids, uint32_t n) {
 // its ids in the kernel's parameter block: nothing is copied to the device.
 // The cardinality is stored by the kernel itself through the staging slot's
 // header (no memset), so such a query is one launch.
+// dense_words = 1 runs the dense counter with one 64-bit word per thread
+// (twice the threads of the pool's shape: more parallelism for few rows).
 int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<uint8_t>& f,
                int path, uint32_t tile_rows, uint64_t* out_words, uint64_t* out_card,
-               cudaStream_t s) {
+               cudaStream_t s, uint32_t dense_words = 0) {
     Pred pred = compile_pred(f.data(), n);
     const bool inl = pred.mode != 2 && n <= kInlineIds;
     const size_t ids_bytes = inl ? 0 : ((size_t)n * 4 + 15) & ~(size_t)15;
@@ -152,10 +154,16 @@ int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<ui
         a.err = p->d_err;
         a.card = card;
         LoopedForm lf{};
+        DenseConfig cfg = p->dense_cfg;
+        if (dense_words == 1) {  // direct loads, 8-byte columns (32-input blocks need two words)
+            cfg.variant = 0;
+            cfg.words_per_thread = 1;
+            if (cfg.adder == 2) cfg.adder = 0;
+        }
         if (looped_form(pred, n, p->looped_max, &lf))
             rc = launch_looped(a, x, lf, p->sm_count, s);
         else
-            rc = launch_dense(a, x, p->dense_cfg, p->sm_count, s);
+            rc = launch_dense(a, x, cfg, p->sm_count, s);
     }
     int rc2 = stage_release(sl, s);
     return rc ? rc : rc2;
@@ -204,11 +212,11 @@ int bm_query_run(bm_pool* p, const bm_query* q, uint64_t* out_card, int32_t* cho
     rc = query_truth(q, f);
     if (rc) return rc;
     BM_CUDA_TRY(cudaSetDevice(p->device));
-    Candidate c{q->path, 0};
+    Candidate c{q->path, 0, 0};
     if (q->path == BM_PATH_AUTO) c = single_query_candidate(p, q->ids, q->n, f);
     if (chosen_path) *chosen_path = c.path;
     return run_single(p, q->ids, q->n, f, c.path, c.tile_rows, q->out_words, out_card,
-                      static_cast<cudaStream_t>(stream));
+                      static_cast<cudaStream_t>(stream), c.dense_words);
 }
 
 int bm_pool_set_sparse_config(bm_pool* p, const bm_sparse_config_t* c) {

@@ -507,7 +507,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
                                    kBatchDenseSpeedup);
             }
         } else {
-            cand[i] = Candidate{qi.path, qi.path == BM_PATH_SPARSE ? p->sparse_cfg.tile_rows : 0u};
+            cand[i] = Candidate{qi.path, qi.path == BM_PATH_SPARSE ? p->sparse_cfg.tile_rows : 0u, 0u};
         }
     }
     if (!auto_idx.empty()) {
@@ -524,7 +524,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
                 dense = dense && p->dense_present[q[i].ids[k]];
             }
             if (c.path == BM_PATH_SPARSE && !lists) c = kCandidateTable[0];
-            if (c.path == BM_PATH_DENSE && !dense) c = Candidate{BM_PATH_SPARSE, p->sparse_cfg.tile_rows};
+            if (c.path == BM_PATH_DENSE && !dense) c = Candidate{BM_PATH_SPARSE, p->sparse_cfg.tile_rows, 0};
             cand[i] = with_rle(p, q[i].ids, q[i].n, c, kBatchDenseSpeedup);
         }
     }

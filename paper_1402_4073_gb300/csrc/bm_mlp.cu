@@ -236,7 +236,9 @@ int bm_query_select(const bm_pool* p, const bm_query* q, int32_t* path, uint32_t
     if (rc) return rc;
     Candidate c = single_query_candidate(p, q->ids, q->n, f);
     *path = c.path;
-    if (tile_rows) *tile_rows = c.tile_rows ? c.tile_rows : p->sparse_cfg.tile_rows;
+    if (tile_rows)
+        *tile_rows = c.path == BM_PATH_SPARSE ? (c.tile_rows ? c.tile_rows : p->sparse_cfg.tile_rows)
+                                              : c.dense_words;
     return BM_OK;
 }
 

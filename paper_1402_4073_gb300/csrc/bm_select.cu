@@ -6,8 +6,11 @@
 
 namespace bm {
 
-const Candidate kCandidateTable[kCandidates] = {
-    {BM_PATH_DENSE, 0}, {BM_PATH_SPARSE, 16384}, {BM_PATH_SPARSE, 32768}, {BM_PATH_SPARSE, 65536}};
+const Candidate kCandidateTable[kCandidates] = {{BM_PATH_DENSE, 0, 0},
+                                                {BM_PATH_SPARSE, 16384, 0},
+                                                {BM_PATH_SPARSE, 32768, 0},
+                                                {BM_PATH_SPARSE, 65536, 0},
+                                                {BM_PATH_DENSE, 0, 1}};
 
 void query_features(const bm_pool* p, const uint32_t* ids, uint32_t n,
                     const std::vector<uint8_t>& f, float out[kFeatures]) {
@@ -44,7 +47,7 @@ Candidate rule_choice(const bm_pool* p, const uint32_t* ids, uint32_t n) {
     for (uint32_t k = 0; k < n; ++k) b += p->list_len[ids[k]];
     const double dense_bytes = (double)n * (double)p->r_bits / 8.0;
     if (!dense || 4.0 * 4.0 * (double)b < dense_bytes)
-        return Candidate{BM_PATH_SPARSE, p->sparse_cfg.tile_rows};
+        return Candidate{BM_PATH_SPARSE, p->sparse_cfg.tile_rows, 0};
     return kCandidateTable[0];
 }
 
@@ -112,7 +115,7 @@ Candidate with_rle(const bm_pool* p, const uint32_t* ids, uint32_t n, Candidate 
     const double rounds = std::ceil(tiles / (4.0 * (double)std::max(1, p->sm_count)));
     if (kRleRoundUs * rounds + kRleUsPerMB * rle_mb <
         (kDenseFixedUs + kDenseUsPerMB * dense_mb) / dense_speedup)
-        return Candidate{BM_PATH_RLE, 0};
+        return Candidate{BM_PATH_RLE, 0, 0};
     return c;
 }
 

@@ -15,10 +15,11 @@ constexpr int kHidden = 64;
 
 // The kernel configurations a query can run on (the selector's outputs).
 struct Candidate {
-    int path;            // BM_PATH_DENSE, BM_PATH_SPARSE or BM_PATH_RLE
-    uint32_t tile_rows;  // sparse tile (0 for dense)
+    int path;              // BM_PATH_DENSE, BM_PATH_SPARSE or BM_PATH_RLE
+    uint32_t tile_rows;    // sparse tile (0 for dense)
+    uint32_t dense_words;  // dense: 1 = one 64-bit word per thread, 0 = the pool's shape
 };
-constexpr int kCandidates = 4;
+constexpr int kCandidates = 5;
 extern const Candidate kCandidateTable[kCandidates];
 
 // Features of a query: log2 n, first transition of f over n, log10 of the

@@ -1,11 +1,12 @@
 """Learned kernel selector: timing collection, training and evaluation.
 
-For every query the library can run one of four candidate kernels
-(``CANDIDATES``: the dense bit-sliced counter, or ScanCount with 16K, 32K or
-64K-row tiles); results are identical, only the time differs.  The paper
-picks among its algorithms by measured time and scores each by its
+For every query the library can run one of five candidate kernels
+(``CANDIDATES``: the dense bit-sliced counter in the pool's shape, ScanCount
+with 16K, 32K or 64K-row tiles, or the dense counter with one 64-bit word per
+thread); results are identical, only the time differs.  The paper picks
+among its algorithms by measured time and scores each by its
 suboptimality, (t - t_best) / t_best (App. C).  Here a small network
-(5 -> 64 -> 64 -> 4, ReLU, fp32) predicts the log time of each candidate
+(5 -> 64 -> 64 -> 5, ReLU, fp32) predicts the log time of each candidate
 from the query's features; the smallest prediction wins.
 
 * ``collect``: time every candidate on every query with the library's own
@@ -51,12 +52,20 @@ def collect(pool: Pool, queries, reps: int = 3, stream=None):
     card = torch.zeros(1, dtype=torch.int64, device=out.device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     saved = pool.configs()["sparse"]
+    saved_dense = pool.configs()["dense"]
     sleep = getattr(torch.cuda, "_sleep", None)
     for c, (path, tile) in enumerate(CANDIDATES):
         if path == PATH_SPARSE:
             if info["lists_loaded"] == 0:
                 continue
             pool.set_sparse_config(tile, saved["threads"], saved["ctas_per_sm"], saved["unroll"])
+        if path == PATH_DENSE:
+            if info["dense_loaded"] == 0:
+                continue
+            d = dict(saved_dense)
+            if tile == 1:  # the one-word-per-thread shape, as the library runs candidate 4
+                d.update(variant=0, words_per_thread=1, adder=0 if d["adder"] == 2 else d["adder"])
+            pool.set_dense_config(**d)
         for i, q in enumerate(queries):
             pq = PreparedQuery(pool, q, out, path)
             pq.run(card, stream)  # warm-up
@@ -70,6 +79,7 @@ def collect(pool: Pool, queries, reps: int = 3, stream=None):
             stream.synchronize()
             times[i, c] = e0.elapsed_time(e1) * 1e3 / reps
     pool.set_sparse_config(**saved)
+    pool.set_dense_config(**saved_dense)
     return feats, times
 
 
@@ -143,10 +153,11 @@ def installed_choices(pool: Pool, queries) -> np.ndarray:
     """Candidate index the pool's installed selector picks for each query
     (the host-side inference that single queries use)."""
     tiles = {tile: c for c, (p, tile) in enumerate(CANDIDATES) if p == PATH_SPARSE}
+    dense = {w: c for c, (p, w) in enumerate(CANDIDATES) if p == PATH_DENSE}
     out = []
     for q in queries:
         path, tile = query_select(pool, q)
-        out.append(0 if path == PATH_DENSE else tiles.get(tile, 2))
+        out.append(dense.get(tile, 0) if path == PATH_DENSE else tiles.get(tile, 2))
     return np.array(out, dtype=np.int64)
 
 

@@ -63,7 +63,7 @@ def test_selector_trains_routes_and_stays_exact(bm, oracle_lib, dg):
         assert set(chosen.tolist()) <= {bm.PATH_DENSE, bm.PATH_SPARSE}
 
 
-def _unpack(params, F=5, H=64, C=4):
+def _unpack(params, F=5, H=64, C=5):
     """The flat fp32 parameter vector as the oracle's W1, b1, W2, b2, W3, b3."""
     from oracle import mlp as omlp
     out, o = [], 0
@@ -94,7 +94,7 @@ def test_host_inference_matches_oracle_network(bm, dg):
     # and deviation as training does, so that the picks differ across queries
     rng = np.random.default_rng(14103)
     parts = []
-    for shp in omlp.shapes():
+    for shp in omlp.shapes(bm.SELECTOR_FEATURES, bm.SELECTOR_HIDDEN, bm.SELECTOR_CANDIDATES):
         parts.append(rng.normal(0.0, 1.0 / np.sqrt(shp[0]), shp).ravel() if len(shp) == 2
                      else np.zeros(shp))
     params = np.concatenate(parts).astype(np.float32)
