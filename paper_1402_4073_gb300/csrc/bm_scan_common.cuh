@@ -173,162 +173,6 @@ __device__ __forceinline__ void count_tile(uint32_t* cnt, uint32_t* scratch, uin
     }
 }
 
-// 16-byte asynchronous copy global -> shared (cp.async, L2 only) and its
-// group bookkeeping.  A thread's copies are complete for that thread after
-// the matching wait; here every lane reads back only what it copied itself.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// count_tile with the loads staged through shared memory and pipelined across
-// the warp's units: vectors are copied by cp.async into `stage` (two windows
-// of W pieces of 32 vectors per warp), each by the lane that will count it,
-// so loads in flight hold no registers; a window is filled from as many of
-// the warp's units as it takes, so the next unit's first loads are in flight
-// while the current unit's last pieces are counted.  The slice bounds of the
-// next unit are loaded ahead (one unit: a warp holds at most two, so units
-// still balance the warps' work).  Arguments, layout and results as
-// count_tile.
-template <int BITS, int W, typename IdOf>
-__device__ __forceinline__ void count_tile_pipe(uint32_t* cnt, uint32_t* scratch, uint4* stage,
-                                                uint32_t* s_next, IdOf id_of, uint32_t n,
-                                                const uint4* vpos, const uint64_t* list_begin,
-                                                const uint32_t* tile_index,
-                                                uint32_t tiles_per_list, uint64_t t0, uint64_t t1,
-                                                uint32_t lo, uint32_t nrows, uint32_t cnt_rows,
-                                                uint32_t d_fill) {
-    constexpr uint32_t kFull = 0xFFFFFFFFu;
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t le = (2u << lane) - 1u, lt = (1u << lane) - 1u;
-    const uint32_t spare = cnt_rows + lane * (32 / BITS);  // this lane's spare counter word
-    const uint32_t ngroups = (n + 31) / 32;
-    uint32_t* ws = scratch + warp * kScanWarpWords;  // [0,32): first vector | zeros bit, [32,64): offset
-    uint4* st = stage + (size_t)warp * (2 * W * 32) + lane;
-    if (threadIdx.x == 0) *s_next = nw;
-    if (d_fill) {  // the rows' counters (those evaluated) start at d_fill
-        const uint32_t fill = BITS == 8 ? d_fill * 0x01010101u : d_fill * 0x00010001u;
-        const uint32_t words = (nrows + 31) / 32 * BITS;  // BITS words per 32 rows
-        for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) cnt[i] = fill;
-    }
-    __syncthreads();
-    auto bounds = [&](uint32_t g, uint32_t& vs, uint32_t& nv) {
-        vs = 0u;
-        nv = 0u;
-        const uint32_t j = g * 32 + lane;
-        if (g < ngroups && j < n) {
-            const uint32_t id = id_of(j);
-            const uint32_t* idx = tile_index + (uint64_t)id * (tiles_per_list + 1);
-            const uint32_t b = __ldg(idx + t0), en = __ldg(idx + t1);
-            const uint64_t begin = __ldg(list_begin + id);
-            const uint64_t base = begin & ~kListComplement;
-            vs = (uint32_t)((base + b) >> 2);
-            nv = b < en ? (uint32_t)((base + en + 3) >> 2) - vs : 0u;
-            vs |= (uint32_t)(begin >> 32) & 0x80000000u;  // bit 31: a list of zeros
-        }
-    };
-    uint32_t team = 1;
-    while (ngroups && team * 2 * ngroups <= nw) team *= 2;
-    const uint32_t units = ngroups * team;
-    auto take = [&]() {  // the warp's next unit (uniform)
-        uint32_t t = 0;
-        if (lane == 0) t = atomicAdd(s_next, 1u);
-        return __shfl_sync(kFull, t, 0);
-    };
-    // the unit being issued (u, its slice table in ws) and the next one
-    uint32_t u = warp, ua = take();
-    uint32_t vs, nv, vsa, nva;
-    bounds(u < units ? u / team : ngroups, vs, nv);
-    bounds(ua < units ? ua / team : ngroups, vsa, nva);
-    uint32_t start = 0, total = 0, mine = 0, member = 0, k = 0;
-    auto setup = [&]() {  // lay unit u's slices end to end in ws
-        __syncwarp();     // the previous unit's lookups are done with ws
-        uint32_t inc = nv;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, inc, o);
-            if (lane >= (uint32_t)o) inc += y;
-        }
-        start = inc - nv;
-        total = __shfl_sync(kFull, inc, 31);
-        const uint32_t ne = __ballot_sync(kFull, nv != 0u);
-        if (nv) {
-            const uint32_t rk = __popc(ne & lt);
-            ws[rk] = vs;
-            ws[32 + rk] = start;
-        }
-        __syncwarp();
-        const uint32_t pieces = (total + 31) / 32;
-        member = u % team;
-        mine = pieces > member ? (pieces - member + team - 1) / team : 0u;
-        k = 0;
-    };
-    auto advance = [&]() {  // move to the next unit, taking one more ahead
-        u = ua;
-        vs = vsa;
-        nv = nva;
-        ua = take();
-        bounds(ua < units ? ua / team : ngroups, vsa, nva);
-        if (u < units) setup();
-    };
-    if (u < units) setup();
-    // fill window buffer buf with the warp's next W pieces, across units;
-    // returns whether any piece was issued (uniform)
-    auto issue = [&](uint32_t buf, uint32_t& valid, uint32_t& subs) {
-        valid = 0u;
-        subs = 0u;
-        bool any = false;
-#pragma unroll
-        for (int i = 0; i < W; ++i) {
-            while (u < units && k >= mine) advance();
-            if (u < units) {  // uniform across the warp
-                const uint32_t q = member + k * team;
-                const uint32_t before = __popc(__ballot_sync(kFull, nv != 0u && start < q * 32));
-                const uint32_t inside = __reduce_or_sync(
-                    kFull, (nv != 0u && (start >> 5) == q) ? (1u << (start & 31)) : 0u);
-                const uint32_t r = before + __popc(inside & le) - 1u;
-                const uint32_t v = q * 32 + lane;
-                if (v < total) {
-                    const uint32_t first = ws[r];
-                    cp_async16(st + (buf * W + i) * 32,
-                               vpos + (first & 0x7FFFFFFFu) + (v - ws[32 + r]));
-                    valid |= 1u << i;
-                    subs |= (first >> 31) << i;
-                }
-                ++k;
-                any = true;
-            }
-        }
-        cp_async_commit();
-        return any;
-    };
-    auto consume = [&](uint32_t buf, uint32_t valid, uint32_t subs) {
-#pragma unroll
-        for (int i = 0; i < W; ++i)
-            if ((valid >> i) & 1u)
-                count_vec<BITS>(cnt, st[(buf * W + i) * 32], lo, nrows, spare, (subs >> i) & 1u);
-    };
-    uint32_t va, sa, vb, sb;
-    bool a_any = issue(0, va, sa);
-    while (a_any) {
-        const bool b_any = issue(1, vb, sb);
-        cp_async_wait<1>();
-        consume(0, va, sa);
-        if (!b_any) break;
-        a_any = issue(0, va, sa);
-        cp_async_wait<1>();
-        consume(1, vb, sb);
-    }
-    cp_async_wait<0>();
-}
-
 // One 32-bit output lane from 32 counters (words cw[0 .. kWords), 16-byte
 // aligned), which are cleared as they are read, ready for the next tile.
 // The words are read 16 bytes at a time; a chunk whose counters are all zero

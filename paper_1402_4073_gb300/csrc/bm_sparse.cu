@@ -43,10 +43,9 @@ __device__ void build_truth(const Pred& pr, uint32_t n, uint32_t* tab, uint32_t 
     }
 }
 
-// Two 512-thread CTAs per SM.  The loads of a warp's pieces go to shared
-// memory (count_tile_pipe), two windows of W pieces in flight per warp,
-// continuing from one unit of lists to the next.
-template <int BITS, int W>  // counter width: 8 or 16; pieces per load window
+// Two 512-thread CTAs per SM: the pipelined loads need the 64 registers
+// that leaves.
+template <int BITS, int U>  // counter width: 8 or 16; pieces per load batch
 __global__ void __launch_bounds__(512, 2)
     scancount_kernel(SparseArgs a, const __grid_constant__ LaunchExtra x) {
     extern __shared__ __align__(16) uint32_t sm[];
@@ -59,7 +58,6 @@ __global__ void __launch_bounds__(512, 2)
     uint32_t* scratch = sm + ((tab_words + 3) & ~3u);
     uint32_t* cnt = scratch + kScanWarpWords * (blockDim.x / 32);
     const uint32_t cnt_words = a.tile_rows / kPer;
-    uint4* stage = reinterpret_cast<uint4*>(cnt + cnt_words + 32);  // past the spare words
     build_truth(a.pred, a.n, tab, tab_words);
 
     const uint64_t ntiles = (a.r_bits + a.tile_rows - 1) / a.tile_rows;
@@ -73,11 +71,11 @@ __global__ void __launch_bounds__(512, 2)
         const uint64_t hi = min(lo + a.tile_rows, a.r_bits);
         const uint64_t t0 = tile * sub;
         const uint64_t t1 = (t0 + sub < a.tiles_per_list) ? t0 + sub : (uint64_t)a.tiles_per_list;
-        count_tile_pipe<BITS, W>(
-            cnt, scratch, stage, &s_next,
-            [&](uint32_t j) { return x.n_inline ? s_ids[j] : __ldg(a.ids + j); }, a.n,
-            reinterpret_cast<const uint4*>(a.positions), a.list_begin, a.tile_index,
-            a.tiles_per_list, t0, t1, (uint32_t)lo, (uint32_t)(hi - lo), a.tile_rows, a.d_fill);
+        count_tile<BITS, U>(cnt, scratch, &s_next,
+                            [&](uint32_t j) { return x.n_inline ? s_ids[j] : __ldg(a.ids + j); }, a.n,
+                            reinterpret_cast<const uint4*>(a.positions),
+                            a.list_begin, a.tile_index, a.tiles_per_list, t0, t1, (uint32_t)lo,
+                            (uint32_t)(hi - lo), a.tile_rows, a.d_fill);
         __syncthreads();
         // 32 rows per thread -> one 32-bit output lane
         const uint32_t lanes = (uint32_t)((hi - lo + 31) / 32);
@@ -113,22 +111,15 @@ int launch_sparse(const SparseArgs& a, const LaunchExtra& x, const SparseConfig&
     const size_t tab_words = ((size_t)(a.n + 1 + 31) / 32 + 3) & ~(size_t)3;
     const int threads = std::max(64, std::min(512, cfg.threads)) & ~31;
     const size_t scratch_words = (size_t)dev::kScanWarpWords * (size_t)(threads / 32);
-    const int window = cfg.unroll <= 2 ? 2 : 4;
-    // counters, one spare word per lane, then each warp's two load windows
-    const size_t stage_words = (size_t)(threads / 32) * 2 * window * 32 * 4;
-    const size_t smem =
-        (tab_words + scratch_words + (size_t)b.tile_rows * bits / 32 + 32 + stage_words) * 4;
+    // counters, then one spare word per lane
+    const size_t smem = (tab_words + scratch_words + (size_t)b.tile_rows * bits / 32 + 32) * 4;
+    const uint64_t ntiles = (b.r_bits + b.tile_rows - 1) / b.tile_rows;
+    const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(ntiles, cap));
     auto go = [&](auto fn) -> int {
         if (smem > 48 * 1024)
             BM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem));
-        // persistent: at most one resident wave
-        int per_sm = 0;
-        BM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
-        if (per_sm < 1) return BM_EINVAL;
-        const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::min(per_sm, std::max(1, cfg.ctas_per_sm));
-        const uint64_t ntiles = (b.r_bits + b.tile_rows - 1) / b.tile_rows;
-        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ntiles, cap));
         fn<<<grid, threads, smem, s>>>(b, x);
         BM_CUDA_TRY(cudaGetLastError());
         return BM_OK;
