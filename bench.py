@@ -235,7 +235,6 @@ def bench_batched(bm, datagen, passes: int = 2, small: bool = False, config: str
     same = bool(torch.equal(cards_plain, cards_batch))
     pool.status()
     logical = sum(query_bytes(q.n, r_bits) for q in queries)
-    l2_gbps = l2_copy_peak()
     # integer roofline: ~2 three-input logic ops per 32-bit input word (one
     # full adder per input in the sideways-sum tree, Sec. 4.3), against
     # SMs x 64 int32 lanes x the maximum SM clock
@@ -254,36 +253,8 @@ def bench_batched(bm, datagen, passes: int = 2, small: bool = False, config: str
             "speedup": round(t_plain / t_batch, 3),
             "plain_logical_GBps": round(logical / t_plain / 1e9, 1),
             "batched_logical_GBps": round(logical / t_batch / 1e9, 1),
-            "l2_roofline": {"bound": "l2", "achieved_GBps": round(logical / t_batch / 1e9, 1),
-                            "peak_GBps": round(l2_gbps, 1),
-                            "frac": round(logical / t_batch / 1e9 / l2_gbps, 4),
-                            "peak_source": "measured here: device copy between two 24 MiB "
-                                           "buffers (L2-resident), read + write bytes, best of 20"},
             "cardinalities_equal": same, "timing": f"best of {passes} passes, CUDA events",
             "autotune": tune}
-
-
-def l2_copy_peak() -> float:
-    """GB/s of a device copy from one 24 MiB buffer to another (48 MiB in all,
-    L2-resident; read + write bytes), best of 20: the bandwidth the batch
-    kernel, whose inputs are served from L2 after the first query of a slab,
-    is held against."""
-    import torch
-    a = torch.empty(6 << 20, dtype=torch.int32, device="cuda").fill_(1)
-    b = torch.empty_like(a)
-    stream = torch.cuda.current_stream()
-    best = 0.0
-    for _ in range(3):
-        b.copy_(a)
-    for _ in range(20):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(10):
-            b.copy_(a)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        best = max(best, 10 * 2 * a.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
-    return best
 
 
 def bench_selector(bm, datagen, n_train: int = 600, small: bool = False):

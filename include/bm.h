@@ -418,10 +418,12 @@ typedef struct bm_server_stats_t {
  * no slot or cannot be allocated.
  *
  * Load shedding (slo_us > 0): the scheduler keeps running estimates of a
- * batch's fixed time and of its time per request (from the batches it ran)
- * and bounds every batch so that its oldest request can still complete
- * within slo_us of its submission; a request that could not complete in time
- * even in a batch of its own is dropped before it runs and completes as
+ * batch's fixed time and of its time per request (from the batches it ran).
+ * A submission is refused (BM_EBUSY) when the requests ahead of it, waiting
+ * and in flight, would not drain within slo_us by those estimates; every
+ * batch is bounded so that its oldest request can still complete within
+ * slo_us of its submission; a waiting request that could not complete in
+ * time even in a batch of its own is dropped before it runs and completes as
  * expired (BM_ETIMEOUT), as with a deadline.  Admitted requests therefore
  * finish near or within the objective under overload instead of queueing
  * without bound.  slo_us = 0 keeps batches of up to max_batch.
@@ -435,7 +437,8 @@ int bm_server_destroy(bm_server* server);
  * Submit a query (its out_words is ignored: the result lives in a server
  * slot) on any path bm_threshold_batch takes.  The query is copied; ids are
  * validated at once for its path (BM_EINVAL, BM_ERANGE).  BM_EBUSY when
- * max_queue requests already wait.  *ticket identifies the request.
+ * max_queue requests already wait, or when the latency objective refuses it
+ * (see bm_server_create).  *ticket identifies the request.
  */
 int bm_server_submit(bm_server* server, const bm_query* q, uint64_t* ticket);
 

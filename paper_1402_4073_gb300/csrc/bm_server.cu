@@ -327,7 +327,15 @@ int bm_server_submit_deadline(bm_server* s, const bm_query* q, uint64_t deadline
     if (deadline_us) r->deadline = r->t_submit + std::chrono::microseconds(deadline_us);
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (s->waiting.size() >= s->cfg.max_queue) {
+        bool refuse = s->waiting.size() >= s->cfg.max_queue;
+        if (s->cfg.slo_us && !refuse) {
+            // admission by the latency objective: the work ahead of this request
+            // (waiting and in flight) must drain within it
+            size_t ahead = s->waiting.size();
+            for (const auto& b : s->batches) ahead += b.reqs.size();
+            refuse = s->est_fixed_us + s->est_per_req_us * (double)(ahead + 1) > s->cfg.slo_us;
+        }
+        if (refuse) {
             s->refused += 1;
             delete r;
             return BM_EBUSY;
