@@ -263,20 +263,10 @@ __global__ void __launch_bounds__(kRleThreads, K <= 9 ? 4 : (K <= 13 ? 3 : 2))
             }
 #pragma unroll
             for (uint32_t u = 0; u < kPer; ++u) {
-                // counted and compacted per warp: one shared atomic per warp, not
-                // one per input on the same two words
                 const uint32_t cls = sum[u] >> 30;
-                const uint32_t m1 = __ballot_sync(0xFFFFFFFFu, cls == kRunClean1);
-                const uint32_t ml = __ballot_sync(0xFFFFFFFFu, cls == kRunLiteral);
-                uint32_t base = 0;
-                if (lane == 0) {
-                    if (m1) atomicAdd(&s_c1, (uint32_t)__popc(m1));
-                    if (ml) base = atomicAdd(&s_nd, (uint32_t)__popc(ml));
-                }
-                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (cls == kRunClean1) atomicAdd(&s_c1, 1u);
                 if (cls == kRunLiteral)
-                    dirty[base + __popc(ml & ((1u << lane) - 1u))] =
-                        make_uint2(id[u], sum[u] & kRunStartMask);
+                    dirty[atomicAdd(&s_nd, 1u)] = make_uint2(id[u], sum[u] & kRunStartMask);
             }
             __syncthreads();
             if (one_chunk) load_sums(m, tile + gridDim.x, sum_next);  // in flight while decoding
