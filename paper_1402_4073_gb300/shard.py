@@ -37,6 +37,22 @@ def shard_words(words: np.ndarray, r_bits: int, rank: int, world: int):
     return np.ascontiguousarray(words[:, row0 // 64:(row1 + 63) // 64]), row1 - row0
 
 
+def shard_positions(flat, offsets, row0: int, row1: int):
+    """The rows [row0, row1) of sorted position lists (list j is
+    flat[offsets[j]:offsets[j+1]]), shifted to start at 0: (flat, offsets)
+    of the rank's lists."""
+    flat = np.asarray(flat, dtype=np.uint32)
+    offsets = np.asarray(offsets, dtype=np.uint64)
+    parts, offs = [], [0]
+    for j in range(len(offsets) - 1):
+        lst = flat[int(offsets[j]):int(offsets[j + 1])]
+        a, b = np.searchsorted(lst, [row0, row1])
+        parts.append(lst[a:b] - np.uint32(row0))
+        offs.append(offs[-1] + int(b - a))
+    local = np.concatenate(parts) if parts else np.zeros(0, dtype=np.uint32)
+    return local, np.asarray(offs, dtype=np.uint64)
+
+
 def _on_device(group) -> bool:
     """True when the group's collectives take CUDA tensors (NCCL)."""
     return dist.get_backend(group) == "nccl"
@@ -132,16 +148,8 @@ class ShardedPool:
         rows, shifted to local row numbers."""
         if self.pool is None:
             return
-        flat = np.asarray(flat, dtype=np.uint32)
-        offsets = np.asarray(offsets, dtype=np.uint64)
-        parts, offs = [], [0]
-        for j in range(len(offsets) - 1):
-            lst = flat[int(offsets[j]):int(offsets[j + 1])]
-            a, b = np.searchsorted(lst, [self.row0, self.row1])
-            parts.append(lst[a:b] - np.uint32(self.row0))
-            offs.append(offs[-1] + int(b - a))
-        local = np.concatenate(parts) if parts else np.zeros(0, dtype=np.uint32)
-        self.pool.put_positions(local, np.asarray(offs, dtype=np.uint64), first_id)
+        local, offs = shard_positions(flat, offsets, self.row0, self.row1)
+        self.pool.put_positions(local, offs, first_id)
 
     def empty_words(self, n: int | None = None) -> torch.Tensor:
         """Device buffer for this rank's part of n output bitmaps."""

@@ -64,3 +64,22 @@ def test_two_rank_row_shards(r_bits):
     for p in procs:
         p.join(timeout=60)
     assert all(ok_words and ok_card for _, ok_words, ok_card in results), results
+
+
+def test_shard_positions_match_shard_words(dg):
+    """The rank's slice of position lists equals the set bits of the rank's
+    slice of the dense words, for every rank of a ragged split."""
+    import __graft_entry__
+    __graft_entry__.cuda_build_module().build()
+    from paper_1402_4073_gb300 import shard
+    r_bits = 64 * 777 + 19
+    words = dg.bernoulli(dg.STREAM_TESTS + 17100, r_bits, np.linspace(0.001, 0.4, 9))
+    flat, offs = dg.positions(words, r_bits)
+    for world in (1, 2, 3, 5):
+        for rank in range(world):
+            local_words, rows = shard.shard_words(words, r_bits, rank, world)
+            lflat, loffs = shard.shard_positions(flat, offs, *shard.row_range(r_bits, rank, world))
+            want_flat, want_offs = dg.positions(local_words, rows) if rows else (
+                np.zeros(0, np.uint32), np.zeros(len(offs), np.uint64))
+            assert np.array_equal(lflat, want_flat), (world, rank)
+            assert np.array_equal(loffs, np.asarray(want_offs, np.uint64)), (world, rank)
