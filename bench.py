@@ -1036,6 +1036,12 @@ def main():
                          f"({64 * nw} rows), {dt:.1f} s"}
         # the oracle's answers of that sample against the timed run's outputs
         checked = oracle_check(bm, outs, cards, answers, nw, words.shape[1])
+        # the same oracle on one host thread, over a smaller prefix
+        oracle.set_threads(1)
+        bps1, nw1, dt1, _ = cpu_sample_time(words, queries, R_BITS, min(4.0, args.cpu_budget))
+        oracle.set_threads(os.cpu_count() or 1)
+        cpu["one_thread"] = {"value": round(bps1 / 1e9, 4), "unit": "GB/s", "cores": 1,
+                             "sample": f"the 4 queries over the first {nw1} words, {dt1:.1f} s"}
 
     extra = {}
     parts = args.parts.split(",")
