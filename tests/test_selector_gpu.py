@@ -28,8 +28,8 @@ def test_selector_trains_routes_and_stays_exact(bm, oracle_lib, dg):
     d = dg.pool_densities(dg.STREAM_TESTS + 14000, n_bm, 1e-5, 3e-2)
     words = dg.bernoulli(dg.STREAM_TESTS + 14001, r_bits, d)
     flat, offs = dg.positions(words, r_bits)
-    train_q = dg.sparse_queries(320, pool=n_bm, nmax=600, stream=dg.STREAM_TESTS + 14002)
-    test_q = dg.sparse_queries(240, pool=n_bm, nmax=600, stream=dg.STREAM_TESTS + 14003)
+    train_q = dg.sparse_queries(600, pool=n_bm, nmax=600, stream=dg.STREAM_TESTS + 14002)
+    test_q = dg.sparse_queries(400, pool=n_bm, nmax=600, stream=dg.STREAM_TESTS + 14003)
     with bm.Pool(r_bits, n_bm) as pool:
         pool.put_dense(words)
         pool.put_positions(flat, offs)
