@@ -418,7 +418,8 @@ typedef struct bm_server_stats_t {
  * no slot or cannot be allocated.
  *
  * Load shedding (slo_us > 0): the scheduler keeps running estimates of a
- * batch's fixed time and of its time per request (from the batches it ran).
+ * batch's fixed time and of its time per input id (a request's work grows
+ * with its number of inputs), from the batches it ran.
  * A submission is refused (BM_EBUSY) when the requests ahead of it, waiting
  * and in flight, would not drain within slo_us by those estimates; every
  * batch is bounded so that its oldest request can still complete within

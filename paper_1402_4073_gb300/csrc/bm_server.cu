@@ -44,6 +44,7 @@ struct Request {
 
 struct Batch {
     Clock::time_point t_launch;
+    uint64_t inputs = 0;  // ids of the batch's requests, repeats counted
     cudaStream_t stream = nullptr;
     uint64_t* d_cards = nullptr;
     uint64_t* h_cards = nullptr;  // pinned
@@ -72,9 +73,11 @@ struct bm_server {
     bool stop = false;
     std::thread th;
 
-    // running estimates of a batch's time: fixed part (from small batches)
-    // and time per request (from large ones), microseconds
-    double est_fixed_us = 100.0, est_per_req_us = 30.0;
+    // running estimates of a batch's time, microseconds: a fixed part (from
+    // batches of few inputs) and a time per input id (from large ones); a
+    // request's work grows with its number of inputs
+    double est_fixed_us = 100.0, est_us_per_input = 0.1;
+    uint64_t waiting_inputs = 0;  // ids of the requests waiting for admission
 
     // statistics
     uint64_t submitted = 0, completed = 0, refused = 0, batches_run = 0, batched_queries = 0;
@@ -101,13 +104,15 @@ void CUDART_CB on_batch_done(void* arg) {
         s->completed += b->reqs.size();
         // the batch's time updates the estimates the latency objective uses
         const double exec = us_since(b->t_launch, now);
-        const double nb = (double)b->reqs.size();
-        if (nb <= 16) {
-            s->est_fixed_us = 0.9 * s->est_fixed_us + 0.1 * exec;
+        const double ni = (double)b->inputs;
+        if (ni <= 2048) {
+            const double fixed = std::max(5.0, exec - s->est_us_per_input * ni);
+            s->est_fixed_us = 0.9 * s->est_fixed_us + 0.1 * fixed;
         } else {
-            const double per = std::max(0.5, (exec - s->est_fixed_us) / nb);
-            s->est_per_req_us = 0.8 * s->est_per_req_us + 0.2 * per;
+            const double per = std::max(1e-3, (exec - s->est_fixed_us) / ni);
+            s->est_us_per_input = 0.8 * s->est_us_per_input + 0.2 * per;
         }
+        b->inputs = 0;
         b->reqs.clear();
         b->busy = false;
     }
@@ -158,12 +163,14 @@ void scheduler(bm_server* s) {
             // finish within it even in a batch of their own
             const auto now = Clock::now();
             const auto slo = std::chrono::microseconds(s->cfg.slo_us);
-            const auto fixed = std::chrono::microseconds((int64_t)(s->est_fixed_us + s->est_per_req_us));
             bool expired = false;
             for (auto it = s->waiting.begin(); it != s->waiting.end();) {
+                const auto alone = std::chrono::microseconds(
+                    (int64_t)(s->est_fixed_us + s->est_us_per_input * (double)(*it)->q.n));
                 if ((*it)->deadline <= now ||
-                    (s->cfg.slo_us && (*it)->t_submit + slo <= now + fixed)) {
+                    (s->cfg.slo_us && (*it)->t_submit + slo <= now + alone)) {
                     Request* r = *it;
+                    s->waiting_inputs -= r->q.n;
                     r->done = true;
                     r->t_launch = r->t_done = now;
                     r->path = BM_ETIMEOUT;
@@ -179,17 +186,22 @@ void scheduler(bm_server* s) {
         for (auto& b : s->batches) {
             if (b.busy || s->waiting.empty() || s->free_slots.empty()) continue;
             // with a latency objective, the batch is sized so that its oldest
-            // request (the front) can still complete within it
-            size_t limit = s->cfg.max_batch;
+            // request (the front) can still complete within it: its inputs'
+            // estimated time fits the front's remaining budget
+            double budget_inputs = 1e300;
             if (s->cfg.slo_us) {
                 const double age = us_since(s->waiting.front()->t_submit, Clock::now());
                 const double budget = (double)s->cfg.slo_us - age - s->est_fixed_us;
-                const double fit = std::floor(budget / s->est_per_req_us);
-                limit = (size_t)std::max(1.0, std::min((double)limit, fit));
+                budget_inputs = budget / s->est_us_per_input;
             }
             std::vector<Request*> take;
-            while (!s->waiting.empty() && !s->free_slots.empty() && take.size() < limit) {
+            double inputs = 0.0;
+            while (!s->waiting.empty() && !s->free_slots.empty() &&
+                   take.size() < s->cfg.max_batch) {
                 Request* r = s->waiting.front();
+                if (!take.empty() && inputs + (double)r->q.n > budget_inputs) break;
+                inputs += (double)r->q.n;
+                s->waiting_inputs -= r->q.n;
                 s->waiting.pop_front();
                 r->slot = s->free_slots.back();
                 s->free_slots.pop_back();
@@ -198,6 +210,7 @@ void scheduler(bm_server* s) {
                 take.push_back(r);
             }
             b.reqs = take;
+            b.inputs = (uint64_t)inputs;
             b.busy = true;
             const auto now = Clock::now();
             b.t_launch = now;
@@ -222,6 +235,7 @@ void scheduler(bm_server* s) {
                     r->path = rc;
                 }
                 b.reqs.clear();
+                b.inputs = 0;
                 b.busy = false;
                 s->cv_done.notify_all();
             } else {
@@ -331,9 +345,9 @@ int bm_server_submit_deadline(bm_server* s, const bm_query* q, uint64_t deadline
         if (s->cfg.slo_us && !refuse) {
             // admission by the latency objective: the work ahead of this request
             // (waiting and in flight) must drain within it
-            size_t ahead = s->waiting.size();
-            for (const auto& b : s->batches) ahead += b.reqs.size();
-            refuse = s->est_fixed_us + s->est_per_req_us * (double)(ahead + 1) > s->cfg.slo_us;
+            uint64_t ahead = s->waiting_inputs + q->n;
+            for (const auto& b : s->batches) ahead += b.inputs;
+            refuse = s->est_fixed_us + s->est_us_per_input * (double)ahead > s->cfg.slo_us;
         }
         if (refuse) {
             s->refused += 1;
@@ -343,6 +357,7 @@ int bm_server_submit_deadline(bm_server* s, const bm_query* q, uint64_t deadline
         r->ticket = s->next_ticket++;
         s->reqs[r->ticket] = r;
         s->waiting.push_back(r);
+        s->waiting_inputs += r->q.n;
         s->submitted += 1;
         *ticket = r->ticket;
     }
@@ -396,6 +411,7 @@ int bm_server_cancel(bm_server* s, uint64_t ticket) {
         auto w = std::find(s->waiting.begin(), s->waiting.end(), r);
         if (w == s->waiting.end()) return BM_EBUSY;  // admitted: it runs to completion
         s->waiting.erase(w);
+        s->waiting_inputs -= r->q.n;
         s->reqs.erase(it);
         s->cancelled += 1;
         delete r;
