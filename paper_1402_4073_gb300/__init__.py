@@ -71,7 +71,10 @@ def words_for(r_bits: int) -> int:
 class Pool:
     """A device-resident pool of `capacity` bitmaps of `r_bits` rows."""
 
-    def __init__(self, r_bits: int, capacity: int, device: int = 0, mem_budget: int = 0):
+    def __init__(self, r_bits: int, capacity: int, device: int | None = None, mem_budget: int = 0):
+        """device: a CUDA device index; by default the current torch device."""
+        if device is None:
+            device = torch.cuda.current_device()
         h = ctypes.c_void_p()
         check(lib.bm_pool_create(device, r_bits, capacity, mem_budget, ctypes.byref(h)),
               "bm_pool_create")

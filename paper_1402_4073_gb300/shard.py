@@ -106,7 +106,8 @@ class ShardedPool:
     holds no pool and contributes nothing."""
 
     def __init__(self, r_bits: int, capacity: int, rank: int | None = None,
-                 world: int | None = None, device: int = 0, mem_budget: int = 0, group=None):
+                 world: int | None = None, device: int | None = None, mem_budget: int = 0,
+                 group=None):
         from . import Pool
         if rank is None or world is None:
             rank = dist.get_rank(group) if dist.is_initialized() else 0
@@ -118,6 +119,7 @@ class ShardedPool:
         self.word0 = self.row0 // 64
         self.words = (self.rows + 63) // 64
         self.pool = Pool(self.rows, capacity, device, mem_budget) if self.rows else None
+        self.device = self.pool.device if self.pool is not None else device
 
     def close(self):
         if self.pool is not None:
@@ -155,7 +157,8 @@ class ShardedPool:
         """Device buffer for this rank's part of n output bitmaps."""
         w = max(1, self.words)
         shape = (w,) if n is None else (n, w)
-        return torch.empty(shape, dtype=torch.int64, device="cuda")
+        dev = "cuda" if self.device is None else f"cuda:{self.device}"
+        return torch.empty(shape, dtype=torch.int64, device=dev)
 
     # -- queries on the local rows -------------------------------------------
 
