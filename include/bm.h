@@ -166,7 +166,9 @@ int bm_pool_bitmap_cardinality(const bm_pool* pool, uint32_t id, uint64_t* out);
 /*
  * Synchronise the pool's device and report device-side failures since the
  * previous call: BM_ETIMEOUT if a kernel's bounded wait expired (its outputs
- * are then undefined), else BM_OK.  Clears the flag.
+ * are then undefined), else BM_OK.  Clears the flag, and after an expired
+ * wait also resets the per-call cardinality accumulators a kernel that gave up
+ * may have left unfinished, so later calls start clean.
  */
 int bm_pool_status(bm_pool* pool);
 
