@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(kBatchThreads, L == 2 ? 3 : 2)
             uint64_t* out = d->out;
             uint32_t P[L][K];
             zero_planes<K, L>(P);
-            count_column<K, G, L>(P, pa.base + W * col, d->ids, d->n, pa.stride_words);
+            count_column<K, G, L, false, true>(P, pa.base + W * col, d->ids, d->n,
+                                                 pa.stride_words);
             const bool vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
             card = finish_column<K, L>(P, pred, pred.table, pa.r_bits, pa.words, out, col, vec_ok);
         }

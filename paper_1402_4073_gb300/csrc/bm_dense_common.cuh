@@ -22,18 +22,29 @@ struct Slice<2> {
     uint32_t v[2];
 };
 
-// Streaming load of one slice (L1 allocation bypassed).
-template <int L>
+// Read-only load of one slice: streaming (L1 allocation bypassed: a single
+// query reads every input word once), or with Cached through L1 (the batch
+// kernel, whose items on one SM read the same slab of the pool for other
+// queries).
+template <int L, bool Cached = false>
 __device__ __forceinline__ Slice<L> ld_slice(const uint64_t* p) {
     Slice<L> s;
     if constexpr (L == 4) {
-        asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                     : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3])
-                     : "l"(p));
+        if constexpr (Cached)
+            asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3])
+                         : "l"(p));
+        else
+            asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3])
+                         : "l"(p));
     } else {
-        asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];"
-                     : "=r"(s.v[0]), "=r"(s.v[1])
-                     : "l"(p));
+        if constexpr (Cached)
+            asm volatile("ld.global.nc.v2.u32 {%0,%1}, [%2];" : "=r"(s.v[0]), "=r"(s.v[1]) : "l"(p));
+        else
+            asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];"
+                         : "=r"(s.v[0]), "=r"(s.v[1])
+                         : "l"(p));
     }
     return s;
 }
@@ -95,8 +106,9 @@ __device__ __forceinline__ uint32_t ld_id(const uint32_t* p) {
 // must be 16-byte aligned: full blocks read their ids four at a time.  The
 // last n mod G inputs go through 8-input blocks padded with zero inputs,
 // which costs less than rippling each input through every plane.  Gen: ids
-// are read with generic loads (they may be in shared memory).
-template <int K, int G, int L, bool Gen = false>
+// are read with generic loads (they may be in shared memory).  Cached: input
+// words through L1 (ld_slice).
+template <int K, int G, int L, bool Gen = false, bool Cached = false>
 __device__ __forceinline__ void count_column(uint32_t (&P)[L][K], const uint64_t* colbase,
                                              const uint32_t* ids, uint32_t n,
                                              uint64_t stride_words) {
@@ -119,7 +131,7 @@ __device__ __forceinline__ void count_column(uint32_t (&P)[L][K], const uint64_t
                 Slice<L> v[16];
 #pragma unroll
                 for (int b = 0; b < 16; ++b)
-                    v[b] = ld_slice<L>(colbase + (uint64_t)id[b] * stride_words);
+                    v[b] = ld_slice<L, Cached>(colbase + (uint64_t)id[b] * stride_words);
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
                     uint32_t x[16];
@@ -145,7 +157,7 @@ __device__ __forceinline__ void count_column(uint32_t (&P)[L][K], const uint64_t
         }
         Slice<L> v[GB];
 #pragma unroll
-        for (int b = 0; b < GB; ++b) v[b] = ld_slice<L>(colbase + (uint64_t)id[b] * stride_words);
+        for (int b = 0; b < GB; ++b) v[b] = ld_slice<L, Cached>(colbase + (uint64_t)id[b] * stride_words);
         add_group<K, L, GB>(P, v);
     }
     while (k < n) {
@@ -154,7 +166,7 @@ __device__ __forceinline__ void count_column(uint32_t (&P)[L][K], const uint64_t
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
             if ((uint32_t)b < m) {
-                v[b] = ld_slice<L>(colbase + (uint64_t)ld_id<Gen>(ids + k + b) * stride_words);
+                v[b] = ld_slice<L, Cached>(colbase + (uint64_t)ld_id<Gen>(ids + k + b) * stride_words);
             } else {
 #pragma unroll
                 for (int l = 0; l < L; ++l) v[b].v[l] = 0u;
