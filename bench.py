@@ -459,11 +459,13 @@ def bench_rle(bm, datagen, reps: int = 10, small: bool = False):
     """Run-length form with clean-run pruning (Sec. 2.1, 4.1) against the dense
     path on the same pools: N = 256 bitmaps of r = 2^26 rows, densities
     max(0.5/k, 1e-4), ones in runs of mean 4096, 256 and 8 rows; the four
-    queries of the main benchmark.  Per pool and query: CUDA-event time per
-    call on each path (median of `reps`), logical input GB/s (N r/8 + r/8 per
+    queries of the main benchmark.  Per pool and query: device time per call
+    on each path (call_times: L2 flushed before each call; and back to back
+    for the run-length path), logical input GB/s (N r/8 + r/8 per
     query), and for the run-length path its algorithmic bytes (the inputs'
-    runs and literal words, 8 bytes each, plus one 4-byte tile summary per
-    input and tile, plus r/8 written) and their fraction of the HBM peak.
+    run-length forms: one 8-byte summary per input and tile and the
+    containers of the mixed tiles; plus r/8 written) and their fraction of
+    the HBM peak.
     small: r = 2^22."""
     import numpy as np
     import torch
@@ -474,7 +476,7 @@ def bench_rle(bm, datagen, reps: int = 10, small: bool = False):
                datagen.Query(ids, datagen.KIND_THRESHOLD, theta=255),
                datagen.Query(ids, datagen.KIND_INTERVAL, lo=2, hi=10)]
     peak, peak_src = peaks()
-    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2
     pools = []
     for mean_run in (4096.0, 256.0, 8.0):
         words = datagen.runs(datagen.STREAM_CONFIG2, r_bits, datagen.config2_density(n), mean_run)
@@ -482,33 +484,24 @@ def bench_rle(bm, datagen, reps: int = 10, small: bool = False):
         pool.put_dense(words)
         del words
         pool.put_rle()
-        runs = lits = 0
+        runs = lits = stored = 0
         for k in range(n):
             a, b = pool.rle_info(k)
-            runs, lits = runs + a, lits + b
-        tiles = (pool.words + 255) // 256
-        alg = 8 * (runs + lits) + 4 * n * tiles + r_bits // 8
+            runs, lits, stored = runs + a, lits + b, stored + pool.rle_bytes(k)
+        # the inputs' run-length forms (summaries, containers) + the output
+        alg = stored + r_bits // 8
         out = pool.empty_words()
         card = torch.zeros(1, dtype=torch.int64, device="cuda")
         rows = []
         for q in queries:
-            t = {}
+            t, hot = {}, {}
             for path in (bm.PATH_DENSE, bm.PATH_RLE):
                 pq = bm.PreparedQuery(pool, q, out, path)
-                for _ in range(3):
-                    pq.run(card)
-                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
-                torch.cuda.synchronize()
-                for i in range(reps):
-                    ev[2 * i].record(stream)
-                    pq.run(card)
-                    ev[2 * i + 1].record(stream)
-                torch.cuda.synchronize()
-                t[path] = statistics.median(ev[2 * i].elapsed_time(ev[2 * i + 1])
-                                            for i in range(reps)) * 1e3
+                t[path], hot[path] = call_times(lambda: pq.run(card), reps, flush)
             logical = query_bytes(n, r_bits)
             rows.append({"query": f"theta={q.theta}" if q.kind == 0 else f"[{q.lo},{q.hi}]",
                          "dense_us": round(t[bm.PATH_DENSE], 1), "rle_us": round(t[bm.PATH_RLE], 1),
+                         "rle_hot_us": round(hot[bm.PATH_RLE], 1),
                          "dense_logical_GBps": round(logical / t[bm.PATH_DENSE] / 1e3, 1),
                          "rle_logical_GBps": round(logical / t[bm.PATH_RLE] / 1e3, 1),
                          "rle_achieved_GBps": round(alg / t[bm.PATH_RLE] / 1e3, 1),
@@ -525,7 +518,9 @@ def bench_rle(bm, datagen, reps: int = 10, small: bool = False):
                         "densities max(0.5/k,1e-4), ones in runs of the given mean length",
             "kernel": "rle_kernel (run-length form, clean-run pruning)",
             "peak": peak, "peak_source": f"hbm_gbs of {peak_src}",
-            "timing": f"median of {reps} calls, CUDA events around each bm_query_run",
+            "timing": f"device time per bm_query_run: median of {reps} calls, each behind a "
+                      "256 MiB fill (L2 flushed, host submission hidden); rle_hot_us: calls back "
+                      "to back",
             "pools": pools}
 
 

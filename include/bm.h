@@ -126,19 +126,25 @@ int bm_pool_put_complement_positions(bm_pool* pool, uint32_t first_id, uint32_t 
 /*
  * Build the run-length form of ids first_id .. first_id + count - 1 from their
  * dense copies (which must be loaded; BM_ERANGE otherwise): the word-aligned
- * run form of a compressed bitmap (Sec. 2.1, EWAH), i.e. maximal runs of
- * all-zero words, all-one words and literal words, kept as a run array, a
- * literal-word array and, per 256-word tile, the run holding the tile's first
- * word.  Queries on BM_PATH_RLE read only the runs and literal words of
- * their inputs.  Synchronous (the words pass through host memory once).
- * Rebuilding an id appends a new form; the earlier one's space is not reused.
- * Errors: BM_ENOMEM over the memory budget.
+ * form of a compressed bitmap (Sec. 2.1, EWAH), in which every 64-bit word is
+ * clean-0 (all zeros), clean-1 (all ones) or literal, kept per 256-word tile:
+ * a tile that one clean run covers is only its class in a summary word; any
+ * other tile is a container of two masks per 32-word slice (literal words,
+ * clean-1 words), the literal ranks of the slices and the tile's literal
+ * words.  Queries on BM_PATH_RLE read only the summaries of their inputs and
+ * the containers of the tiles where an input mixes kinds.  Synchronous (the
+ * words pass through host memory once).  Rebuilding an id appends a new form;
+ * the earlier one's space is not reused.  Errors: BM_ENOMEM over the memory
+ * budget.
  */
 int bm_pool_put_rle(bm_pool* pool, uint32_t first_id, uint32_t count);
 
-/* Runs (without the terminating sentinel) and literal words of id's
- * run-length form.  BM_ERANGE if the id has none. */
-int bm_pool_rle_info(const bm_pool* pool, uint32_t id, uint64_t* runs, uint64_t* literal_words);
+/* Statistics of id's run-length form: maximal runs of words of one kind
+ * (clean-0, clean-1, literal), literal words, and the device bytes of its
+ * form (containers and one 4-byte summary per tile).  Any pointer may be
+ * NULL.  BM_ERANGE if the id has none. */
+int bm_pool_rle_info(const bm_pool* pool, uint32_t id, uint64_t* runs, uint64_t* literal_words,
+                     uint64_t* device_bytes);
 
 typedef struct bm_pool_info_t {
     uint64_t r_bits;           /* rows per bitmap */

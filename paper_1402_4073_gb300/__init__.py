@@ -133,19 +133,27 @@ class Pool:
               "bm_pool_put_positions")
 
     def put_rle(self, first_id: int = 0, count: int | None = None) -> None:
-        """Build the run-length form (clean/literal word runs) of dense ids
-        first_id .. first_id + count - 1 (all loaded dense ids from first_id by
-        default) for BM_PATH_RLE queries."""
+        """Build the run-length form (clean-0 / clean-1 / literal words, per
+        256-word tile) of dense ids first_id .. first_id + count - 1 (all
+        loaded dense ids from first_id by default) for BM_PATH_RLE queries."""
         if count is None:
             count = self.info()["capacity"] - first_id
         check(lib.bm_pool_put_rle(self.handle, first_id, count), "bm_pool_put_rle")
 
+    def _rle_stats(self, id_: int) -> tuple[int, int, int]:
+        r, l, b = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib.bm_pool_rle_info(self.handle, id_, ctypes.byref(r), ctypes.byref(l),
+                                   ctypes.byref(b)), "bm_pool_rle_info")
+        return int(r.value), int(l.value), int(b.value)
+
     def rle_info(self, id_: int) -> tuple[int, int]:
-        """(runs, literal words) of id's run-length form."""
-        r, l = ctypes.c_uint64(), ctypes.c_uint64()
-        check(lib.bm_pool_rle_info(self.handle, id_, ctypes.byref(r), ctypes.byref(l)),
-              "bm_pool_rle_info")
-        return int(r.value), int(l.value)
+        """(runs, literal words) of id's run-length form: maximal runs of
+        words of one kind, and the words that are neither all 0 nor all 1."""
+        return self._rle_stats(id_)[:2]
+
+    def rle_bytes(self, id_: int) -> int:
+        """Device bytes of id's run-length form (containers and summaries)."""
+        return self._rle_stats(id_)[2]
 
     def info(self) -> dict:
         i = _native.bm_pool_info_t()

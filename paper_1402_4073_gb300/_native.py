@@ -70,7 +70,7 @@ SIGNATURES = {
     "bm_pool_info": (i32, [vp, ctypes.POINTER(bm_pool_info_t)]),
     "bm_pool_put_rle": (i32, [vp, u32, u32]),
     "bm_weighted_threshold": (i32, [vp, ctypes.POINTER(bm_weighted_query), vp, vp]),
-    "bm_pool_rle_info": (i32, [vp, u32, P64, P64]),
+    "bm_pool_rle_info": (i32, [vp, u32, P64, P64, P64]),
     "bm_pool_bitmap_cardinality": (i32, [vp, u32, P64]),
     "bm_pool_status": (i32, [vp]),
     "bm_pool_set_dense_config": (i32, [vp, ctypes.POINTER(bm_dense_config_t)]),

@@ -126,13 +126,11 @@ int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<ui
         rc = launch_sparse(a, x, p->sparse_cfg, p->sm_count, s);
     } else if (path == BM_PATH_RLE) {
         RleArgs a{};
-        a.runs = p->d_runs;
-        a.lits = p->d_lits;
-        a.run_begin = p->d_run_begin;
-        a.lit_begin = p->d_lit_begin;
-        a.run_count = p->d_run_count;
+        a.arena = reinterpret_cast<const uint8_t*>(p->d_rle_arena);
+        a.base = p->d_rle_base;
         a.tile_index = p->d_rle_tiles;
-        a.tiles_plus_one = p->rle_tiles + 1;
+        a.capacity = p->capacity;
+        a.err = p->d_err;
         a.words = p->words;
         a.r_bits = p->r_bits;
         a.ids = d_ids;

@@ -633,13 +633,11 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
     // to the cardinalities the graph zeroed
     for (uint32_t i : rle_list) {
         RleArgs a{};
-        a.runs = p->d_runs;
-        a.lits = p->d_lits;
-        a.run_begin = p->d_run_begin;
-        a.lit_begin = p->d_lit_begin;
-        a.run_count = p->d_run_count;
+        a.arena = reinterpret_cast<const uint8_t*>(p->d_rle_arena);
+        a.base = p->d_rle_base;
         a.tile_index = p->d_rle_tiles;
-        a.tiles_plus_one = p->rle_tiles + 1;
+        a.capacity = p->capacity;
+        a.err = p->d_err;
         a.words = p->words;
         a.r_bits = p->r_bits;
         a.ids = hd[i].ids;

@@ -194,24 +194,23 @@ int launch_k(const DenseArgs& a, const LaunchExtra& x, const DenseConfig& cfg, i
                             : cfg.adder == 2 ? csa_direct_kernel<K, G32, 4>
                                              : csa_direct_kernel<K, 16, 4>)
                          : (cfg.adder == 1 ? csa_direct_kernel<K, 8, 2> : csa_direct_kernel<K, 16, 2>);
-        if (tab_bytes > 48 * 1024)
-            BM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tab_bytes));
+        const int rc = ensure_smem_limit((const void*)fn, tab_bytes);
+        if (rc) return rc;
         fn<<<grid, threads, tab_bytes, s>>>(a, x);
         BM_CUDA_TRY(cudaGetLastError());
         return BM_OK;
     }
-    int dev = 0, optin = 0;
-    BM_CUDA_TRY(cudaGetDevice(&dev));
-    BM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    int optin = 0;
+    const int orc = smem_optin(&optin);
+    if (orc) return orc;
     auto run = [&](auto fn, int nt) -> int {
         // stages of 16 bitmaps x nt 16-byte slices, plus two mbarriers each
         const int fit = (int)(((size_t)optin - tab_bytes) / ((size_t)256 * nt + 16));
         const int stages = std::max(2, std::min({8, cfg.stages, fit}));
         if (fit < 2) return BM_EINVAL;
         const size_t bytes = (size_t)stages * 16 * nt * 16 + 2 * (size_t)stages * 8 + tab_bytes;
-        BM_CUDA_TRY(
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        const int rc = ensure_smem_limit((const void*)fn, bytes);
+        if (rc) return rc;
         const uint64_t ntiles = (ncols + nt - 1) / nt;
         const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);
         const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(ntiles, cap));

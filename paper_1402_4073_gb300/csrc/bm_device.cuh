@@ -312,6 +312,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// Global -> shared copy of 8 bytes by one thread (cp.async, generic proxy);
+// the thread's copies since the last commit form one group.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// Wait until at most N of the thread's groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Sum of a per-thread value over the warp.
 __device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
     return __reduce_add_sync(0xFFFFFFFFu, v);

@@ -141,41 +141,47 @@ struct SparseConfig {
 int launch_sparse(const SparseArgs& a, const LaunchExtra& x, const SparseConfig& cfg, int sm_count,
                   cudaStream_t s);
 
-// Word-aligned run-length form of a bitmap (EWAH-like, Sec. 2.1): maximal
-// runs of all-zero words, all-one words or literal words.  A run is a uint2:
-// x = first word | type << 30, y = index of its first literal word among the
-// bitmap's literals (literal runs).  Each bitmap's runs end with a sentinel
-// run starting at word ceil(r/64).
-constexpr uint32_t kRunClean0 = 0, kRunClean1 = 1, kRunLiteral = 2;
-constexpr uint32_t kRunStartMask = (1u << 30) - 1u;
-constexpr uint32_t kRleTileWords = 256;  // words per tile of the run index and kernel
+// Word-aligned run-length form of a bitmap (EWAH-like, Sec. 2.1), tiled for
+// the GPU: every word is clean-0 (all zeros), clean-1 (all ones) or literal.
+// Per tile of kRleTileWords words, one summary (uint2): x = the tile's class
+// (clean-0 or clean-1 when one clean run covers it, else mixed) << 30 | the
+// offset, in 16-byte units from the bitmap's base in the container arena, of
+// a mixed tile's container; y = the container's size in 16-byte units.  A
+// container (16-byte aligned, padded to 16 bytes) is: L[0..7] (32-bit; bit b
+// of L[s]: word 32 s + b is literal), O[0..7] (bit b of O[s]: that word is
+// clean-1), R[0..7] (bytes; R[s]: literal words in slices before s), 8 bytes
+// of padding, then the tile's literal words in order.  Summaries are stored
+// tile-major (tile t of id j at t * capacity + j), so a tile's summaries of
+// consecutive ids are adjacent.
+constexpr uint32_t kTileClean0 = 0, kTileClean1 = 1, kTileMixed = 2;
+constexpr uint32_t kTileOffsetMask = (1u << 30) - 1u;
+constexpr uint32_t kRleTileWords = 256;   // words per tile of the summaries and kernel
+constexpr uint32_t kRleSliceWords = 32;   // words per mask of a container (one per warp)
+constexpr uint32_t kRleHeaderBytes = 80;  // container bytes before the literal words
 
 // Arguments of one run-length query launch.
 struct RleArgs {
-    const uint2* runs;            // pool run arena
-    const uint64_t* lits;         // pool literal arena
-    const uint64_t* run_begin;    // device, per id: first run in the arena
-    const uint64_t* lit_begin;    // device, per id: first literal in the arena
-    const uint32_t* run_count;    // device, per id: runs including the sentinel
-    const uint32_t* tile_index;   // device, per id: tiles + 1 summaries: run holding the tile's
-                                  // first word | class << 30 (clean-0 / clean-1 over the whole
-                                  // tile, else literal: to be decoded)
-    uint32_t tiles_plus_one;
+    const uint8_t* arena;         // pool container arena (16-byte aligned)
+    const uint64_t* base;         // device, per id: the id's first arena unit (16 bytes)
+    const uint2* tile_index;      // device, tiles x capacity summaries (tile-major)
+    uint32_t capacity;            // summaries between consecutive tiles
     uint64_t words, r_bits;
     const uint32_t* ids;
     uint32_t n;
     Pred pred;
     uint64_t* out;
     unsigned long long* card;    // as DenseArgs
+    int* err;                    // pool error word (bounded waits)
 };
 
 int launch_rle(const RleArgs& a, const LaunchExtra& x, int sm_count, cudaStream_t s);
-// Run-length encoding of `words` words (host): runs (with the sentinel),
-// literal words, and the summary of every kRleTileWords-word tile (tiles + 1
-// entries): index of the run holding its first word | class << 30, the class
-// being the run's type when that clean run covers the tile, else literal.
-void rle_encode(const uint64_t* words, uint64_t nwords, std::vector<uint2>& runs,
-                std::vector<uint64_t>& lits, std::vector<uint32_t>& tile_index);
+// Run-length form of `nwords` words (host): the containers of the mixed tiles
+// (appended to `containers`, 16-byte units; offsets relative to its size on
+// entry) and one summary per tile (written to summary[0], summary[stride],
+// ...).  Also counts the maximal runs of equal word kind and the literal
+// words.
+void rle_encode(const uint64_t* words, uint64_t nwords, std::vector<uint4>& containers,
+                uint2* summary, size_t stride, uint64_t* runs, uint64_t* literal_words);
 int launch_cardinality(const uint64_t* words, uint64_t r_bits, unsigned long long* out,
                        int sm_count, cudaStream_t s);
 int planes_for(uint32_t n);  // counter planes needed for counts 0..n
@@ -223,18 +229,16 @@ struct bm_pool {
     uint64_t* d_list_begin = nullptr;     // per id, device copy
     uint32_t tiles_per_list = 0;
 
-    // run-length form: growable run and literal arenas, per-id tile index
-    uint2* d_runs = nullptr;
-    uint64_t runs_cap = 0, runs_used = 0;
-    uint64_t* d_lits = nullptr;
-    uint64_t lits_cap = 0, lits_used = 0;
-    uint64_t* d_run_begin = nullptr;      // per id, device
-    uint64_t* d_lit_begin = nullptr;      // per id, device
-    uint32_t* d_run_count = nullptr;      // per id, device
-    uint32_t* d_rle_tiles = nullptr;      // capacity * (rle_tiles + 1)
+    // run-length form: one growable container arena, per-id bases, tile-major
+    // summaries
+    uint4* d_rle_arena = nullptr;
+    uint64_t rle_cap = 0, rle_used = 0;   // arena 16-byte units allocated / in use
+    uint64_t* d_rle_base = nullptr;       // per id, device
+    uint2* d_rle_tiles = nullptr;         // rle_tiles x capacity
     uint32_t rle_tiles = 0;               // ceil(words / kRleTileWords)
     std::vector<uint8_t> rle_present;
-    std::vector<uint64_t> rle_runs, rle_lits;  // host: per id runs and literal words
+    std::vector<uint64_t> rle_runs, rle_lits;  // host, per id: runs and literal words
+    std::vector<uint64_t> rle_units;           // host, per id: container 16-byte units
 
     int* d_err = nullptr;
     static constexpr int kSlots = 8;
@@ -266,5 +270,12 @@ int stage_commit(bm_stage_slot* slot, size_t bytes, cudaStream_t s);
 int stage_release(bm_stage_slot* slot, cudaStream_t s);
 int track_alloc(bm_pool* p, void** ptr, size_t bytes);
 void track_free(bm_pool* p, void* ptr, size_t bytes);
+// Raise kernel fn's dynamic shared-memory limit on the current device to at
+// least `bytes`.  The runtime is called only when a launch needs more than
+// any earlier one of fn on that device (the call costs more than a small
+// query's kernel).
+int ensure_smem_limit(const void* fn, size_t bytes);
+// Largest dynamic shared memory a CTA may opt in to on the current device.
+int smem_optin(int* bytes);
 void batch_state_free(bm_pool* p);
 }  // namespace bm

@@ -5,6 +5,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "bm_device.cuh"
 
@@ -16,6 +19,31 @@ void bm_note_cuda_error(cudaError_t e, const char* what, const char* file, int l
 }
 
 namespace bm {
+
+int ensure_smem_limit(const void* fn, size_t bytes) {
+    if (bytes <= 48 * 1024) return BM_OK;  // no opt-in needed
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> raised;
+    int dev = 0;
+    BM_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& have = raised[std::make_pair(fn, dev)];
+    if (bytes <= have) return BM_OK;
+    BM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    have = bytes;
+    return BM_OK;
+}
+
+int smem_optin(int* bytes) {
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> cached[kMaxDevices];
+    int dev = 0;
+    BM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < kMaxDevices && (*bytes = cached[dev].load()) > 0) return BM_OK;
+    BM_CUDA_TRY(cudaDeviceGetAttribute(bytes, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (dev >= 0 && dev < kMaxDevices) cached[dev].store(*bytes);
+    return BM_OK;
+}
 
 int track_alloc(bm_pool* p, void** ptr, size_t bytes) {
     if (p->mem_budget && p->device_bytes + bytes > p->mem_budget) return BM_ENOMEM;
@@ -222,6 +250,7 @@ int bm_pool_create(int device, uint64_t r_bits, uint32_t capacity, uint64_t mem_
     p->rle_present.assign(capacity, 0);
     p->rle_runs.assign(capacity, 0);
     p->rle_lits.assign(capacity, 0);
+    p->rle_units.assign(capacity, 0);
     *out = p;
     return BM_OK;
 }
@@ -241,8 +270,7 @@ int bm_pool_destroy(bm_pool* p) {
     if (p->d_pos) cudaFree(p->d_pos);
     if (p->d_tile_index) cudaFree(p->d_tile_index);
     if (p->d_list_begin) cudaFree(p->d_list_begin);
-    for (void* q : {(void*)p->d_runs, (void*)p->d_lits, (void*)p->d_run_begin, (void*)p->d_lit_begin,
-                    (void*)p->d_run_count, (void*)p->d_rle_tiles})
+    for (void* q : {(void*)p->d_rle_arena, (void*)p->d_rle_base, (void*)p->d_rle_tiles})
         if (q) cudaFree(q);
     delete p;
     return BM_OK;

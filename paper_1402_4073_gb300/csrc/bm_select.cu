@@ -95,25 +95,27 @@ Candidate select_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
     return best < 0 ? kCandidateTable[0] : kCandidateTable[best];
 }
 
-// Cost of a single query on GB300, fitted to the measured kernels (N = 256,
-// r = 2^26): the dense counter streams its bytes at the HBM rate; the
-// run-length kernel pays a latency chain of about 6 us per round of tiles
-// across the GPU (four CTAs per SM, one tile each) plus about 1.6 us per MB
-// of runs, literal words and tile summaries (runs of mean 4096, 256 and 8
-// rows: 51, 130 and 650 us against about 42 + 1.6 x 6.4, 34.6 and 380 MB).
-constexpr double kDenseUsPerMB = 0.145, kDenseFixedUs = 5.0;
-constexpr double kRleUsPerMB = 1.6, kRleRoundUs = 6.0;
+// Cost of a single query on GB300 (device time with L2 flushed), fitted to
+// the measured kernels: the dense counter streams N r/8 bytes at about
+// 7 TB/s after a fixed 9 us (N = 16..256, r = 2^20..2^26); the run-length
+// kernel pays about 12.5 us of launch and set-up, 1.3 us per round of tiles
+// across the GPU (three CTAs per SM below 8192 inputs, two above) and 1.05 us
+// per MB of summaries and containers read (N = 32..256, r = 2^20..2^26, runs
+// of mean 4096, 256 and 8 rows: 13-299 us).
+constexpr double kDenseUsPerMB = 0.14, kDenseFixedUs = 9.0;
+constexpr double kRleUsPerMB = 1.05, kRleRoundUs = 1.3, kRleFixedUs = 12.5;
 
 Candidate with_rle(const bm_pool* p, const uint32_t* ids, uint32_t n, Candidate c,
                    double dense_speedup) {
     if (c.path != BM_PATH_DENSE || !all_have(p->rle_present, ids, n)) return c;
-    uint64_t words = 0;  // runs and literal words, 8 bytes each
-    for (uint32_t k = 0; k < n; ++k) words += p->rle_runs[ids[k]] + p->rle_lits[ids[k]];
+    uint64_t units = 0;  // container bytes (masks and literal words) / 16
+    for (uint32_t k = 0; k < n; ++k) units += p->rle_units[ids[k]];
     const double tiles = (double)((p->words + kRleTileWords - 1) / kRleTileWords);
-    const double rle_mb = (8.0 * (double)words + 4.0 * (double)n * tiles) / 1e6;
+    const double rle_mb = (16.0 * (double)units + 8.0 * (double)n * tiles) / 1e6;
     const double dense_mb = (double)n * (double)p->r_bits / 8.0 / 1e6;
-    const double rounds = std::ceil(tiles / (4.0 * (double)std::max(1, p->sm_count)));
-    if (kRleRoundUs * rounds + kRleUsPerMB * rle_mb <
+    const double per_sm = n < 8192 ? 3.0 : 2.0;
+    const double rounds = std::ceil(tiles / (per_sm * (double)std::max(1, p->sm_count)));
+    if (kRleFixedUs + kRleRoundUs * rounds + kRleUsPerMB * rle_mb <
         (kDenseFixedUs + kDenseUsPerMB * dense_mb) / dense_speedup)
         return Candidate{BM_PATH_RLE, 0, 0};
     return c;

@@ -117,9 +117,8 @@ int launch_sparse(const SparseArgs& a, const LaunchExtra& x, const SparseConfig&
     const uint64_t cap = (uint64_t)sm_count * (uint64_t)std::max(1, cfg.ctas_per_sm);
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(ntiles, cap));
     auto go = [&](auto fn) -> int {
-        if (smem > 48 * 1024)
-            BM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem));
+        const int rc = ensure_smem_limit((const void*)fn, smem);
+        if (rc) return rc;
         fn<<<grid, threads, smem, s>>>(b, x);
         BM_CUDA_TRY(cudaGetLastError());
         return BM_OK;

@@ -133,24 +133,23 @@ def test_rle_clustered_workload_subset(bm, oracle_lib, dg):
 
 
 def _rle_wins(pool, ids, dense_speedup):
-    """The library's run-length cost model (GB300 fit): about 6 us per round
-    of 256-word tiles over four CTAs per SM plus 1.6 us per MB of runs,
-    literal words and tile summaries, against 5 us plus 0.145 us per MB of
-    dense words, divided by dense_speedup."""
+    """The library's run-length cost model (GB300 fit, device time per query):
+    12.5 us plus 1.3 us per round of 256-word tiles over three CTAs per SM
+    plus 1.05 us per MB of summaries and containers, against 9 us plus
+    0.14 us per MB of dense words, divided by dense_speedup."""
     info = pool.info()
-    words = sum(sum(pool.rle_info(int(i))) for i in ids)
+    stored = sum(pool.rle_bytes(int(i)) for i in ids)
     tiles = (info["words"] + 255) // 256
-    rle_mb = (8.0 * words + 4.0 * len(ids) * tiles) / 1e6
     dense_mb = len(ids) * info["r_bits"] / 8.0 / 1e6
-    rounds = -(-tiles // (4 * info["sm_count"]))
-    return 6.0 * rounds + 1.6 * rle_mb < (5.0 + 0.145 * dense_mb) / dense_speedup
+    rounds = -(-tiles // (3 * info["sm_count"]))
+    return 12.5 + 1.3 * rounds + 1.05 * stored / 1e6 < (9.0 + 0.14 * dense_mb) / dense_speedup
 
 
 def test_rle_auto_selection(bm, oracle_lib, dg):
     """BM_PATH_AUTO takes the run-length path for a query over clustered
     inputs (few runs) and the dense counter over incompressible ones, alone
     and in a batch, with the same answers as the oracle either way."""
-    r_bits = 1 << 23
+    r_bits = 1 << 25
     clustered = dg.runs(dg.STREAM_TESTS + 20400, r_bits, np.linspace(0.01, 0.3, 48), 4096.0)
     scattered = dg.bernoulli(dg.STREAM_TESTS + 20401, r_bits, np.linspace(0.2, 0.5, 48))
     words = np.concatenate([clustered, scattered])
