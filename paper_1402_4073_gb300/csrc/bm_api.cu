@@ -127,7 +127,6 @@ int run_single(bm_pool* p, const uint32_t* ids, uint32_t n, const std::vector<ui
     } else if (path == BM_PATH_RLE) {
         RleArgs a{};
         a.arena = reinterpret_cast<const uint8_t*>(p->d_rle_arena);
-        a.base = p->d_rle_base;
         a.tile_index = p->d_rle_tiles;
         a.capacity = p->capacity;
         a.err = p->d_err;

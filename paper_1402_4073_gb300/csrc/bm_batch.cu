@@ -634,7 +634,6 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
     for (uint32_t i : rle_list) {
         RleArgs a{};
         a.arena = reinterpret_cast<const uint8_t*>(p->d_rle_arena);
-        a.base = p->d_rle_base;
         a.tile_index = p->d_rle_tiles;
         a.capacity = p->capacity;
         a.err = p->d_err;

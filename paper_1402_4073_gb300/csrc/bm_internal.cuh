@@ -143,18 +143,24 @@ int launch_sparse(const SparseArgs& a, const LaunchExtra& x, const SparseConfig&
 
 // Word-aligned run-length form of a bitmap (EWAH-like, Sec. 2.1), tiled for
 // the GPU: every word is clean-0 (all zeros), clean-1 (all ones) or literal.
-// Per tile of kRleTileWords words, one summary (uint2): x = the tile's class
-// (clean-0 or clean-1 when one clean run covers it, else mixed) << 30 | the
-// offset, in 16-byte units from the bitmap's base in the container arena, of
-// a mixed tile's container; y = the container's size in 16-byte units.  A
-// container (16-byte aligned, padded to 16 bytes) is: L[0..7] (32-bit; bit b
-// of L[s]: word 32 s + b is literal), O[0..7] (bit b of O[s]: that word is
-// clean-1), R[0..7] (bytes; R[s]: literal words in slices before s), 8 bytes
-// of padding, then the tile's literal words in order.  Summaries are stored
+// Per tile of kRleTileWords words, one summary (uint2): the tile's class
+// (clean-0 or clean-1 when one clean run covers it, else mixed) and, for a
+// mixed tile, where its container starts in the pool's container arena, in
+// 16-byte units (bits 0..29 in x below the class, bits 30.. in y above the
+// container's size in 16-byte units, which is at most 133).  A container
+// (16-byte aligned, padded to 16 bytes) is: L[0..7] (32-bit; bit b of L[s]:
+// word 32 s + b is literal), O[0..7] (bit b of O[s]: that word is clean-1),
+// R[0..7] (bytes; R[s]: literal words in slices before s), 8 bytes of
+// padding, then the tile's literal words in order.  Summaries are stored
 // tile-major (tile t of id j at t * capacity + j), so a tile's summaries of
 // consecutive ids are adjacent.
 constexpr uint32_t kTileClean0 = 0, kTileClean1 = 1, kTileMixed = 2;
 constexpr uint32_t kTileOffsetMask = (1u << 30) - 1u;
+// Container start (16-byte units) and size (16-byte units) of a summary.
+__host__ __device__ inline uint64_t tile_container(uint2 s) {
+    return ((uint64_t)(s.y >> 8) << 30) | (s.x & kTileOffsetMask);
+}
+__host__ __device__ inline uint32_t tile_units(uint2 s) { return s.y & 0xFFu; }
 constexpr uint32_t kRleTileWords = 256;   // words per tile of the summaries and kernel
 constexpr uint32_t kRleSliceWords = 32;   // words per mask of a container (one per warp)
 constexpr uint32_t kRleHeaderBytes = 80;  // container bytes before the literal words
@@ -162,7 +168,6 @@ constexpr uint32_t kRleHeaderBytes = 80;  // container bytes before the literal 
 // Arguments of one run-length query launch.
 struct RleArgs {
     const uint8_t* arena;         // pool container arena (16-byte aligned)
-    const uint64_t* base;         // device, per id: the id's first arena unit (16 bytes)
     const uint2* tile_index;      // device, tiles x capacity summaries (tile-major)
     uint32_t capacity;            // summaries between consecutive tiles
     uint64_t words, r_bits;
@@ -176,12 +181,13 @@ struct RleArgs {
 
 int launch_rle(const RleArgs& a, const LaunchExtra& x, int sm_count, cudaStream_t s);
 // Run-length form of `nwords` words (host): the containers of the mixed tiles
-// (appended to `containers`, 16-byte units; offsets relative to its size on
-// entry) and one summary per tile (written to summary[0], summary[stride],
-// ...).  Also counts the maximal runs of equal word kind and the literal
-// words.
+// (appended to `containers`) and one summary per tile (written to
+// summary[0], summary[stride], ...), whose container starts count from
+// `first_unit` for the arena unit where `containers` will be placed.  Also
+// counts the maximal runs of equal word kind and the literal words.
 void rle_encode(const uint64_t* words, uint64_t nwords, std::vector<uint4>& containers,
-                uint2* summary, size_t stride, uint64_t* runs, uint64_t* literal_words);
+                uint64_t first_unit, uint2* summary, size_t stride, uint64_t* runs,
+                uint64_t* literal_words);
 int launch_cardinality(const uint64_t* words, uint64_t r_bits, unsigned long long* out,
                        int sm_count, cudaStream_t s);
 int planes_for(uint32_t n);  // counter planes needed for counts 0..n
@@ -233,7 +239,6 @@ struct bm_pool {
     // summaries
     uint4* d_rle_arena = nullptr;
     uint64_t rle_cap = 0, rle_used = 0;   // arena 16-byte units allocated / in use
-    uint64_t* d_rle_base = nullptr;       // per id, device
     uint2* d_rle_tiles = nullptr;         // rle_tiles x capacity
     uint32_t rle_tiles = 0;               // ceil(words / kRleTileWords)
     std::vector<uint8_t> rle_present;

@@ -270,7 +270,7 @@ int bm_pool_destroy(bm_pool* p) {
     if (p->d_pos) cudaFree(p->d_pos);
     if (p->d_tile_index) cudaFree(p->d_tile_index);
     if (p->d_list_begin) cudaFree(p->d_list_begin);
-    for (void* q : {(void*)p->d_rle_arena, (void*)p->d_rle_base, (void*)p->d_rle_tiles})
+    for (void* q : {(void*)p->d_rle_arena, (void*)p->d_rle_tiles})
         if (q) cudaFree(q);
     delete p;
     return BM_OK;

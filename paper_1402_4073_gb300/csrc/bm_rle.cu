@@ -32,8 +32,9 @@
 
 namespace bm {
 
-void rle_encode(const uint64_t* w, uint64_t nw, std::vector<uint4>& containers, uint2* summary,
-                size_t stride, uint64_t* runs, uint64_t* literal_words) {
+void rle_encode(const uint64_t* w, uint64_t nw, std::vector<uint4>& containers,
+                uint64_t first_unit, uint2* summary, size_t stride, uint64_t* runs,
+                uint64_t* literal_words) {
     auto kind = [](uint64_t x) -> uint32_t {
         return x == 0ull ? kTileClean0 : (x == ~0ull ? kTileClean1 : kTileMixed);
     };
@@ -79,11 +80,12 @@ void rle_encode(const uint64_t* w, uint64_t nw, std::vector<uint4>& containers, 
             sum = make_uint2(kTileClean1 << 30, 0u);
             continue;
         }
-        // header and literal words, padded to 16 bytes.  A bitmap has at most
-        // 2^18 tiles of at most 133 units: offsets stay below 2^30.
+        // header and literal words, padded to 16 bytes (at most 133 units)
         const size_t units = (kRleHeaderBytes + 8 * lits.size() + 15) / 16;
         const uint64_t at = containers.size();
-        sum = make_uint2((kTileMixed << 30) | (uint32_t)(at - base), (uint32_t)units);
+        const uint64_t start = first_unit + (at - base);
+        sum = make_uint2((kTileMixed << 30) | (uint32_t)(start & kTileOffsetMask),
+                         (uint32_t)((start >> 30) << 8) | (uint32_t)units);
         containers.resize(at + units, make_uint4(0u, 0u, 0u, 0u));
         uint8_t* c = reinterpret_cast<uint8_t*>(containers.data() + at);
         uint8_t R[kSlices];
@@ -201,8 +203,7 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2)
     uint64_t* empty = full + kRleStages;
     RleStage* desc = reinterpret_cast<RleStage*>(empty + kRleStages);   // [stages]
     uint64_t* list_at = reinterpret_cast<uint64_t*>(desc + kRleStages);  // [chunk]: arena bytes
-    uint64_t* s_base = list_at + kRleChunk;                              // [chunk]: per input
-    uint32_t* s_ids = reinterpret_cast<uint32_t*>(s_base + kRleChunk);   // [chunk]
+    uint32_t* s_ids = reinterpret_cast<uint32_t*>(list_at + kRleChunk);  // [chunk]
     uint16_t* list_units = reinterpret_cast<uint16_t*>(s_ids + kRleChunk);  // [chunk]
     uint2* s_sum = reinterpret_cast<uint2*>(list_units + kRleChunk);      // [ahead][256]
     uint32_t* tab = reinterpret_cast<uint32_t*>(s_sum + kRleAhead * 256);  // f over 0..n
@@ -210,14 +211,11 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2)
     const uint32_t below = (1u << lane) - 1u;
     const uint32_t tab_words = a.pred.mode == 2 ? (a.n + 1 + 31) / 32 : 0u;
     for (uint32_t w = tid; w < tab_words; w += kRleThreads) tab[w] = a.pred.table[w];
-    // with one chunk (n <= kRleChunk) the ids and arena bases are read once
+    // with one chunk (n <= kRleChunk) the ids are read once
     const bool one_chunk = a.n <= kRleChunk;
     if (one_chunk)
-        for (uint32_t i = tid; i < a.n; i += kRleThreads) {
-            const uint32_t id = x.n_inline ? x.inl[i] : __ldg(a.ids + i);
-            s_ids[i] = id;
-            s_base[i] = __ldg(a.base + id);
-        }
+        for (uint32_t i = tid; i < a.n; i += kRleThreads)
+            s_ids[i] = x.n_inline ? x.inl[i] : __ldg(a.ids + i);
     if (tid == 0) {
         for (uint32_t s = 0; s < kRleStages; ++s) {
             mbar_init(&full[s], 1);
@@ -273,7 +271,6 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2)
                     // eight inputs per lane in flight; with one chunk the first
                     // 256 were loaded while the previous tile was posted
                     uint2 sm[8];
-                    uint32_t idv[8];
                     if (one_chunk && k0 == 0) {
                         const uint32_t slot = ti % kRleAhead;
                         cp_async_wait<kRleAhead - 1>();
@@ -284,13 +281,12 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2)
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
                             const uint32_t i = k0 + 32 * u + lane;
-                            idv[u] = 0u;
                             sm[u] = make_uint2(0u, 0u);  // clean-0: nothing to add
                             if (i < m) {
-                                idv[u] = one_chunk ? s_ids[i]
-                                         : x.n_inline ? x.inl[c0 + i]
-                                                      : __ldg(a.ids + c0 + i);
-                                sm[u] = __ldg(row + idv[u]);
+                                const uint32_t id = one_chunk      ? s_ids[i]
+                                                    : x.n_inline ? x.inl[c0 + i]
+                                                                 : __ldg(a.ids + c0 + i);
+                                sm[u] = __ldg(row + id);
                             }
                         }
                     }
@@ -323,10 +319,8 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2)
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
                             if ((sm[u].x >> 30) == kTileMixed) {
-                                const uint32_t i = k0 + 32 * u + lane;
-                                const uint64_t b = one_chunk ? s_base[i] : __ldg(a.base + idv[u]);
-                                list_at[at] = (b + (sm[u].x & kTileOffsetMask)) * 16;
-                                list_units[at] = (uint16_t)sm[u].y;
+                                list_at[at] = tile_container(sm[u]) * 16;
+                                list_units[at] = (uint16_t)tile_units(sm[u]);
                                 ++at;
                             }
                         }
@@ -505,7 +499,7 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2)
 }
 
 constexpr size_t kRleFixedSmem = (size_t)kRleStages * (kRleStageBytes + 16 + sizeof(RleStage)) +
-                                 (size_t)kRleChunk * (8 + 8 + 4 + 2) +
+                                 (size_t)kRleChunk * (8 + 4 + 2) +
                                  (size_t)kRleAhead * 256 * 8;
 constexpr size_t kRleMaxSmem = kRleFixedSmem + ((size_t)BM_N_MAX + 1 + 31) / 32 * 4;
 constexpr int kRleMaxDevices = 64;
@@ -572,12 +566,10 @@ int bm_pool_put_rle(bm_pool* p, uint32_t first_id, uint32_t count) {
     std::lock_guard<std::mutex> lk(p->mu);
     BM_CUDA_TRY(cudaSetDevice(p->device));
     const uint64_t tiles = p->rle_tiles;
-    if (!p->d_rle_base) {
+    if (!p->d_rle_tiles) {
         const size_t sum_bytes = (size_t)p->capacity * std::max<uint64_t>(tiles, 1) * 8;
-        int rc = track_alloc(p, (void**)&p->d_rle_base, (size_t)p->capacity * 8);
-        if (!rc) rc = track_alloc(p, (void**)&p->d_rle_tiles, sum_bytes);
+        const int rc = track_alloc(p, (void**)&p->d_rle_tiles, sum_bytes);
         if (rc) return rc;
-        BM_CUDA_TRY(cudaMemset(p->d_rle_base, 0, (size_t)p->capacity * 8));
         BM_CUDA_TRY(cudaMemset(p->d_rle_tiles, 0, sum_bytes));
     }
     // grow the container arena to hold `need` 16-byte units
@@ -597,7 +589,7 @@ int bm_pool_put_rle(bm_pool* p, uint32_t first_id, uint32_t count) {
     // ids in batches: a batch's summaries are one strided copy into the
     // tile-major summary matrix
     constexpr uint32_t kBatch = 64;
-    std::vector<uint64_t> host(p->words), bases(kBatch), runs(kBatch), lits(kBatch), units(kBatch);
+    std::vector<uint64_t> host(p->words), runs(kBatch), lits(kBatch), units(kBatch);
     std::vector<uint4> cont;
     std::vector<uint2> sums((size_t)tiles * kBatch);
     for (uint32_t j0 = 0; j0 < count; j0 += kBatch) {
@@ -607,13 +599,13 @@ int bm_pool_put_rle(bm_pool* p, uint32_t first_id, uint32_t count) {
             BM_CUDA_TRY(cudaMemcpy(host.data(), p->d_dense + (uint64_t)id * p->stride_words,
                                    p->words * 8, cudaMemcpyDeviceToHost));
             cont.clear();
-            rle_encode(host.data(), p->words, cont, sums.data() + j, nb, &runs[j], &lits[j]);
+            rle_encode(host.data(), p->words, cont, p->rle_used, sums.data() + j, nb, &runs[j],
+                       &lits[j]);
             int rc = grow(p->rle_used + cont.size());
             if (rc) return rc;
             if (!cont.empty())
                 BM_CUDA_TRY(cudaMemcpy(p->d_rle_arena + p->rle_used, cont.data(),
                                        cont.size() * 16, cudaMemcpyHostToDevice));
-            bases[j] = p->rle_used;
             units[j] = cont.size();
             p->rle_used += cont.size();
         }
@@ -622,8 +614,6 @@ int bm_pool_put_rle(bm_pool* p, uint32_t first_id, uint32_t count) {
             BM_CUDA_TRY(cudaMemcpy2D(p->d_rle_tiles + id0, (size_t)p->capacity * 8, sums.data(),
                                      (size_t)nb * 8, (size_t)nb * 8, tiles,
                                      cudaMemcpyHostToDevice));
-        BM_CUDA_TRY(cudaMemcpy(p->d_rle_base + id0, bases.data(), (size_t)nb * 8,
-                               cudaMemcpyHostToDevice));
         for (uint32_t j = 0; j < nb; ++j) {
             p->rle_runs[id0 + j] = runs[j];
             p->rle_lits[id0 + j] = lits[j];
