@@ -218,3 +218,54 @@ def test_rle_errors(bm, dg):
         assert e.value.code == bm.BM_ERANGE
         with pytest.raises(bm.BMError):
             pool.rle_info(3)
+
+
+def _tiled_bytes(words: np.ndarray) -> int:
+    """Device bytes of the tiled run-length form, restated here: an 8-byte
+    summary per 256-word tile, and for a tile that is neither all clean-0 nor
+    all clean-1 words a container of 80 header bytes plus 8 per literal word,
+    padded to 16 bytes."""
+    ones = np.uint64(0xFFFFFFFFFFFFFFFF)
+    total = 0
+    for t0 in range(0, len(words), 256):
+        w = words[t0:t0 + 256]
+        lit = int(np.count_nonzero((w != 0) & (w != ones)))
+        total += 8
+        if lit == 0 and (np.all(w == 0) or np.all(w == ones)):
+            continue
+        total += (80 + 8 * lit + 15) // 16 * 16
+    return total
+
+
+def test_rle_form_sizes_rebuild_and_growth(bm, oracle_lib, dg):
+    """The form's size matches its definition word by word (ragged last tile,
+    tiles that are one clean run, literal-only tiles); forms built by several
+    calls over different id ranges (each call's summaries land in its own
+    columns of the tile-major matrix), an id rebuilt after the others (its
+    old form left behind), and queries across all of them keep the oracle's
+    answers."""
+    r_bits = 256 * 64 * 7 + 64 * 37 + 11  # seven full tiles and a ragged eighth
+    nw = (r_bits + 63) // 64
+    words = _mixed_words(dg, r_bits, dg.STREAM_TESTS + 20500)
+    full = np.full(nw, np.uint64(0xFFFFFFFFFFFFFFFF))
+    full[-1] = np.uint64((1 << (r_bits % 64)) - 1)
+    blocky = np.zeros(nw, np.uint64)  # whole tiles of ones, zeros, literals
+    blocky[0:256] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    blocky[512:768] = np.uint64(0x5555555555555555)
+    blocky[1024:1100] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    words = np.concatenate([words, full[None, :], blocky[None, :]])
+    n_bm = words.shape[0]
+    with bm.Pool(r_bits, n_bm) as pool:
+        pool.put_dense(words)
+        pool.put_rle(0, 3)
+        pool.put_rle(3, n_bm - 3)
+        pool.put_rle(1, 1)  # rebuilt: appended after the others
+        for k in range(n_bm):
+            assert pool.rle_bytes(k) == _tiled_bytes(words[k]), k
+            assert pool.rle_info(k) == _runs_of(words[k]), k
+        ids = np.arange(n_bm, dtype=np.uint32)
+        for q in (dg.Query(ids, 0, theta=1), dg.Query(ids, 0, theta=3), dg.Query(ids, 1, lo=2, hi=4),
+                  dg.Query(np.array([1, 1, 7, 8, 8], dtype=np.uint32), 0, theta=3)):
+            got = _run(bm, pool, q, bm.PATH_RLE)
+            want = oracle_lib.query(words, q, r_bits)
+            assert np.array_equal(got[0], want[0]) and got[1] == want[1], q
