@@ -11,14 +11,15 @@
 // (k in the paper), a mixed one is listed.  When the predicate takes one
 // value over every count the tile can still reach, [c1, c1 + mixed inputs],
 // the tile is that value: the producer writes it and nothing else is read.
-// Otherwise the producer
-// streams the mixed inputs' containers (masks, ranks, literal words) into a
-// ring of shared-memory stages with bulk copies (TMA, one mbarrier per
-// stage), up to 32 per stage, and runs ahead into the next tiles while the
-// consumers work (it also loads the next tile's summaries while posting this
-// one).  A consumer warp first finds which containers of the stage have a
-// word of its slice that is not zero; a lane then reads its word of each of
-// them from shared memory (the literal at the slice's rank plus the lane's
+// Otherwise the producer streams the mixed inputs' containers (masks, ranks,
+// literal words) into a ring of shared-memory stages, up to 32 per stage, one
+// lane per container issuing 16-byte asynchronous copies (cp.async) whose
+// completion the stage's mbarrier tracks, and runs ahead into the next tiles
+// while the consumers work (it also loads the next tiles' summaries while
+// posting this one).  Containers are a few hundred bytes: the lanes' copies
+// issue faster than one bulk copy (TMA) per container.  A consumer warp first
+// finds which containers of the stage have a word of its slice that is not
+// zero; a lane then reads its word of each of them from shared memory (the literal at the slice's rank plus the lane's
 // place among the literal bits, or all ones), the words go through the
 // eight-input sideways-sum block of the dense counter, and at the tile's
 // last stage the predicate is evaluated on count + c1.  Only summaries and
@@ -104,6 +105,19 @@ void rle_encode(const uint64_t* w, uint64_t nw, std::vector<uint4>& containers,
 namespace {
 
 using namespace dev;
+
+// Global -> shared copy of 16 bytes by one thread, cached in L2 only.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+// Arrive on `bar` once every cp.async this thread issued so far has landed;
+// the arrival counts against the barrier's expected count.
+__device__ __forceinline__ void cp_async_mbar_arrive_noinc(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
 
 constexpr uint32_t kRleSlices = kRleTileWords / kRleSliceWords;  // consumer warps
 constexpr uint32_t kRleThreads = kRleTileWords + 32;             // + the producer warp
@@ -218,7 +232,9 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2)
             s_ids[i] = x.n_inline ? x.inl[i] : __ldg(a.ids + i);
     if (tid == 0) {
         for (uint32_t s = 0; s < kRleStages; ++s) {
-            mbar_init(&full[s], 1);
+            // full: each producer lane's copies (tracked by cp.async) and the
+            // post of the stage's descriptor
+            mbar_init(&full[s], 33);
             mbar_init(&empty[s], kRleSlices);
         }
         fence_barrier_init();
@@ -230,7 +246,6 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2)
         // producer: classify each tile's inputs; write a constant tile, or
         // post its mixed inputs' containers in stages (the tile's last is
         // marked), then a terminal stage
-        const uint64_t pol = policy_evict_first();  // a query reads each container once
         // with one chunk, the summaries of the first 256 inputs of the next
         // kRleAhead tiles are in flight to s_sum (a lane copies its own eight)
         auto fetch_first = [&](uint64_t tile, uint32_t slot) {
@@ -365,23 +380,23 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2)
                     }
                     const uint32_t count =
                         __popc(__ballot_sync(0xFFFFFFFFu, valid && incl * 16 <= kRleStageBytes));
-                    const uint32_t bytes =
-                        16 * __shfl_sync(0xFFFFFFFFu, incl, count ? count - 1 : 0) * (count != 0);
                     const uint32_t off = 16 * (incl - units);
                     RleStage& d = desc[st];
-                    if (lane < count) d.off[lane] = (uint16_t)off;
+                    if (lane < count) {
+                        d.off[lane] = (uint16_t)off;
+                        const uint8_t* src = a.arena + list_at[e + lane];
+                        uint8_t* dst = ring + st * kRleStageBytes + off;
+                        for (uint32_t q = 0; q < units; ++q) cp_async16(dst + 16 * q, src + 16 * q);
+                    }
+                    cp_async_mbar_arrive_noinc(&full[st]);
                     __syncwarp();
                     if (lane == 0) {
                         d.tile = (uint32_t)tile;
                         d.count = count;
                         d.last = final && e + count >= nd;
                         d.c1 = c1;
-                        mbar_arrive_expect_tx(&full[st], bytes);
+                        mbar_arrive(&full[st]);
                     }
-                    __syncwarp();
-                    if (lane < count)
-                        bulk_g2s(ring + st * kRleStageBytes + off, a.arena + list_at[e + lane],
-                                 16 * units, &full[st], pol);
                     __syncwarp();
                     e += count;
                     ++it;
@@ -393,10 +408,12 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2)
         // the terminal stage
         if (ok && free_stage((uint32_t)(it % kRleStages))) {
             const uint32_t st = (uint32_t)(it % kRleStages);
+            cp_async_mbar_arrive_noinc(&full[st]);
+            __syncwarp();
             if (lane == 0) {
                 desc[st].tile = kRleNoTile;
                 desc[st].count = 0;
-                mbar_arrive_expect_tx(&full[st], 0);
+                mbar_arrive(&full[st]);
             }
             ++it;
         }
