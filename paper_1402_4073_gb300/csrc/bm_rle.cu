@@ -348,15 +348,29 @@ __global__ void __launch_bounds__(kRleThreads, K <= 13 ? 3 : 2)
                     if (konst >= 0) {
                         // the whole tile is one value: the producer writes it,
                         // the consumers never see the tile
+                        const uint64_t w0 = tile * kRleTileWords;
+                        const uint64_t fill = konst ? ~0ull : 0ull;
+                        if (w0 + kRleTileWords <= a.words &&
+                            (reinterpret_cast<uintptr_t>(a.out) & 15u) == 0) {
+                            // a whole tile: two words per 16-byte store
 #pragma unroll
-                        for (uint32_t u = 0; u < kRleTileWords / 32; ++u) {
-                            const uint64_t col = tile * kRleTileWords + 32 * u + lane;
-                            if (col < a.words) {
-                                uint64_t word = konst ? ~0ull : 0ull;
-                                if (col == a.words - 1 && (a.r_bits & 63u))
-                                    word &= (1ull << (a.r_bits & 63u)) - 1ull;
-                                a.out[col] = word;
-                                card += (unsigned long long)__popcll(word);
+                            for (uint32_t u = 0; u < kRleTileWords / 64; ++u)
+                                asm volatile("st.global.v2.u64 [%0], {%1, %2};" ::"l"(
+                                                 a.out + w0 + 64 * u + 2 * lane),
+                                             "l"(fill), "l"(fill)
+                                             : "memory");
+                            if (konst && lane == 0) card += 64ull * kRleTileWords;
+                        } else {
+#pragma unroll
+                            for (uint32_t u = 0; u < kRleTileWords / 32; ++u) {
+                                const uint64_t col = w0 + 32 * u + lane;
+                                if (col < a.words) {
+                                    uint64_t word = fill;
+                                    if (col == a.words - 1 && (a.r_bits & 63u))
+                                        word &= (1ull << (a.r_bits & 63u)) - 1ull;
+                                    a.out[col] = word;
+                                    card += (unsigned long long)__popcll(word);
+                                }
                             }
                         }
                         break;

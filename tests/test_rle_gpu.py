@@ -269,3 +269,36 @@ def test_rle_form_sizes_rebuild_and_growth(bm, oracle_lib, dg):
             got = _run(bm, pool, q, bm.PATH_RLE)
             want = oracle_lib.query(words, q, r_bits)
             assert np.array_equal(got[0], want[0]) and got[1] == want[1], q
+
+
+def test_rle_constant_tiles_aligned_and_unaligned_output(bm, oracle_lib, dg):
+    """Tiles that RBMrg's pruning settles (whole tiles of one value) are
+    written whole by 16-byte stores into an aligned output and word by word
+    into one that is only 8-byte aligned, and around a ragged last tile;
+    both give the oracle's words and cardinality, with nothing written past
+    the buffer."""
+    r_bits = 256 * 64 * 6 + 64 * 5 + 9
+    nw = (r_bits + 63) // 64
+    ones = np.uint64(0xFFFFFFFFFFFFFFFF)
+    words = np.zeros((6, nw), np.uint64)
+    words[0:3, : 256 * 3] = ones  # three inputs all ones over the first three tiles
+    words[3, 256 * 4:256 * 5] = np.uint64(0x00FF00FF00FF00FF)
+    words[4:6] = dg.runs(dg.STREAM_TESTS + 20600, r_bits, np.array([0.02, 0.2]), 4096.0)
+    words[:, -1] &= np.uint64((1 << (r_bits % 64)) - 1)
+    ids = np.arange(6, dtype=np.uint32)
+    with _pool(bm, words, r_bits) as pool:
+        for q in (dg.Query(ids, 0, theta=3), dg.Query(ids, 0, theta=0), dg.Query(ids, 0, theta=1),
+                  dg.Query(ids, 1, lo=0, hi=2)):
+            want = oracle_lib.query(words, q, r_bits)
+            for shift in (0, 1):
+                big = torch.full((pool.words + 2,), -7, dtype=torch.int64, device="cuda")
+                out = big[shift:shift + pool.words]
+                card = torch.zeros(1, dtype=torch.int64, device="cuda")
+                assert bm.query_run(pool, q, out, card, path=bm.PATH_RLE) == bm.PATH_RLE
+                torch.cuda.synchronize()
+                pool.status()
+                assert np.array_equal(bm.to_numpy_words(out), want[0]), (q, shift)
+                assert int(card.item()) == want[1], (q, shift)
+                if shift:
+                    assert int(big[0].item()) == -7
+                assert int(big[shift + pool.words].item()) == -7
