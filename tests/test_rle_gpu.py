@@ -93,7 +93,8 @@ def test_rle_matches_oracle(bm, oracle_lib, dg, r_bits):
 
 def test_rle_many_inputs_and_clean_ones(bm, oracle_lib, dg):
     """n = 2500 (three classification passes of 1024) with a third of the
-    inputs all ones: thresholds below, at and above the clean-one count."""
+    inputs all ones: thresholds below, at and above the clean-one count, an
+    interval and a table predicate."""
     r_bits = 16384 * 5 + 77
     nw = (r_bits + 63) // 64
     base = dg.runs(dg.STREAM_TESTS + 20100, r_bits, np.linspace(0.001, 0.7, 60), 2000.0)
@@ -116,6 +117,12 @@ def test_rle_many_inputs_and_clean_ones(bm, oracle_lib, dg):
         # same answers on the dense path
         dense = _run(bm, pool, q, bm.PATH_DENSE)
         assert np.array_equal(dense[0], got[0]) and dense[1] == got[1]
+        # a table predicate over the three passes (many transitions, f(0) = 1)
+        f = (np.arange(n + 1) % 7) < 3
+        q = dg.Query(ids, 2, table=dg.table_from_bools(f))
+        got = _run(bm, pool, q, bm.PATH_RLE)
+        want = oracle_lib.query(words, q, r_bits)
+        assert np.array_equal(got[0], want[0]) and got[1] == want[1], "table"
 
 
 def test_rle_clustered_workload_subset(bm, oracle_lib, dg):
