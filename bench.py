@@ -257,6 +257,46 @@ def bench_batched(bm, datagen, passes: int = 2, small: bool = False, config: str
             "autotune": tune}
 
 
+def bench_selector_clustered(bm, datagen, small: bool = False):
+    """The selector with the run-length path among its candidates: a pool of
+    five blocks of bitmaps whose ones come in runs of mean 8 .. 16384 rows
+    (dense words, position lists and run-length forms of all), each query's
+    ids from one block.  Trained on its own timings of separate training
+    queries; time lost on the test queries for the network, for the library's
+    rule without a network (density rule, then the run-length cost model)
+    and for fixed candidates, and how often each candidate is the fastest and
+    the network's pick."""
+    import numpy as np
+    from paper_1402_4073_gb300 import selector
+    r_bits, nbm, nq = ((1 << 20), 200, 150) if small else ((1 << 22), 400, 300)
+    words, flat, offs, _ = datagen.clustered_pool(nbm, r_bits)
+    test_q = datagen.clustered_queries(nq, nbm)
+    train_q = datagen.clustered_queries(nq, nbm, stream=datagen.STREAM_CLUSTERED + (7 << 36))
+    pool = bm.Pool(r_bits, nbm)
+    pool.put_dense(words)
+    pool.put_positions(flat, offs)
+    pool.put_rle()
+    del words, flat
+    tune = pool.autotune()
+    ftr, ttr = selector.collect(pool, train_q, reps=3)
+    fte, tte = selector.collect(pool, test_q, reps=3)
+    model = selector.train(ftr, ttr, steps=3000)
+    res = selector.evaluate(pool, model, test_q, fte, tte)
+    pool.status()
+    pool.close()
+    out = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in res.items()}
+    out.update({"workload": f"clustered: {nbm} x 2^{r_bits.bit_length() - 1} pool, five blocks "
+                            "with runs of mean 8..16384 rows (densities log-uniform [1e-4,0.5]; "
+                            f"dense + lists + run-length forms), {nq} queries from one block "
+                            "each, N log-uniform [2,block], theta<=min(N,64), 10% intervals",
+                "candidates": ["dense", "sparse16k", "sparse32k", "sparse64k", "dense1w", "rle"],
+                "fastest_choices": np.bincount(np.nanargmin(tte, axis=1),
+                                               minlength=bm.SELECTOR_CANDIDATES).tolist(),
+                "train_queries": nq, "final_train_loss": round(model.final_loss, 5),
+                "autotune": tune})
+    return out
+
+
 def bench_selector(bm, datagen, n_train: int = 600, small: bool = False):
     """Sparse workload (5000 x 2^24, dense + lists; 2000 queries): train the
     selector on its own timings of separate training queries, then report
@@ -1055,6 +1095,7 @@ def main():
         extra["batched"] = bench_batched(bm, datagen, small=args.small, config=args.batch_config)
     if "selector" in parts:
         extra["selector"] = bench_selector(bm, datagen, small=args.small)
+        extra["selector"]["clustered"] = bench_selector_clustered(bm, datagen, small=args.small)
     if "serving" in parts:
         extra["serving"] = bench_serving(bm, datagen, small=args.small)
 

@@ -23,6 +23,9 @@ Workload recipes (bitmaps of r rows as ceil(r/64) little-endian uint64 words):
 * ``sparse_pool`` / ``sparse_queries``: 5000 x 2^24, densities log-uniform in
   [1e-5, 1e-2], each bitmap also as a sorted uint32 position list; N
   log-uniform in [2, 4096], theta uniform in [1, min(N, 64)].
+* ``clustered_pool`` / ``clustered_queries``: five blocks of bitmaps whose ones
+  come in runs of mean 8 .. 16384 rows, densities log-uniform in [1e-4, 0.5],
+  with position lists; each query takes its ids from one block.
 * ``serving_pool`` / ``serving_queries``: 10000 x 2^22, densities log-uniform in
   [1e-5, 0.5]; N log-uniform in [2, 4096], theta uniform in [1, N], Poisson
   arrival times at a given rate.
@@ -49,6 +52,7 @@ STREAM_CONFIG2 = 2 << 40
 STREAM_MIXED = 3 << 40
 STREAM_SPARSE = 4 << 40
 STREAM_SERVING = 5 << 40
+STREAM_CLUSTERED = 6 << 40
 STREAM_TESTS = 9 << 40
 _QUERY_OFFSET = 1 << 32  # query-parameter streams sit above the bitmap streams
 
@@ -263,6 +267,42 @@ def sparse_pool(n_bitmaps: int = 5000, r_bits: int = 1 << 24):
 def sparse_queries(n_queries: int = 2000, pool: int = 5000, nmin: int = 2, nmax: int = 4096,
                    stream: int = STREAM_SPARSE + _QUERY_OFFSET):
     return _queries(stream, n_queries, pool, nmin, nmax, 64, 0.0)
+
+
+CLUSTERED_RUNS = (8.0, 64.0, 512.0, 4096.0, 16384.0)
+
+
+def clustered_pool(n_bitmaps: int = 400, r_bits: int = 1 << 22):
+    """Bitmaps in five equal blocks of ids whose ones come in runs of mean
+    length 8, 64, 512, 4096 and 16384 rows (geometric, at uniform starts),
+    densities log-uniform in [1e-4, 0.5]; with their position lists."""
+    d = pool_densities(STREAM_CLUSTERED + _QUERY_OFFSET - 1, n_bitmaps, 1e-4, 0.5)
+    words = np.empty((n_bitmaps, words_for(r_bits)), dtype=np.uint64)
+    per = n_bitmaps // len(CLUSTERED_RUNS)
+    for g, mean in enumerate(CLUSTERED_RUNS):
+        lo = g * per
+        hi = n_bitmaps if g == len(CLUSTERED_RUNS) - 1 else lo + per
+        words[lo:hi] = runs(STREAM_CLUSTERED + lo, r_bits, d[lo:hi], mean)
+    flat, offs = positions(words, r_bits)
+    return words, flat, offs, d
+
+
+def clustered_queries(n_queries: int = 300, pool: int = 400, nmin: int = 2, nmax: int = 400,
+                      stream: int = STREAM_CLUSTERED + _QUERY_OFFSET):
+    """Queries over one block of clustered_pool each (blocks in turn): N
+    log-uniform in [nmin, min(nmax, block)], theta uniform in [1, min(N, 64)],
+    an interval with probability 0.1."""
+    groups = len(CLUSTERED_RUNS)
+    per = pool // groups
+    by_group = [_queries(stream + (g << 32), (n_queries + groups - 1) // groups, per, nmin,
+                         min(nmax, per), 64, 0.1) for g in range(groups)]
+    out = []
+    for i in range(n_queries):
+        g = i % groups
+        q = by_group[g][i // groups]
+        q.ids = (q.ids + np.uint32(g * per)).astype(np.uint32)
+        out.append(q)
+    return out
 
 
 def serving_pool(n_bitmaps: int = 10000, r_bits: int = 1 << 22):

@@ -508,31 +508,39 @@ int bm_server_stats(bm_server* server, bm_server_stats_t* out);
  * ---------------------------------------------------------------------- */
 
 /* Number of selector features and candidates (the network's in/outputs). */
-#define BM_SELECTOR_FEATURES 5u
+#define BM_SELECTOR_FEATURES 6u
 #define BM_SELECTOR_HIDDEN 64u
-#define BM_SELECTOR_CANDIDATES 5u
+#define BM_SELECTOR_CANDIDATES 6u
 /*
  * Candidate c runs: 0 = dense counter in the pool's shape; 1, 2, 3 = ScanCount
  * with tiles of 16384, 32768, 65536 rows; 4 = dense counter with one 64-bit
  * word per thread (direct loads, twice the threads: for queries whose rows
- * leave the pool's shape short of parallelism).  In a batch, candidates 0 and
- * 4 both run in the batch's dense kernel.
+ * leave the pool's shape short of parallelism); 5 = the run-length path.  In
+ * a batch, candidates 0 and 4 both run in the batch's dense kernel, and the
+ * run-length candidate, which runs as a launch of its own, is taken over a
+ * dense pick only if its predicted time beats the dense one divided by the
+ * batch's measured gain (2.5): a query left in the dense kernel shares the
+ * pool's reads with the others.
  */
 
 /*
- * Features of a query (5 floats, host): log2 n; the first count where f
+ * Features of a query (6 floats, host): log2 n; the first count where f
  * changes, divided by n (theta / n for a threshold); log10 of the mean and of
- * the largest input density (cardinality / r, floored at 1e-9); log2 r.
+ * the largest input density (cardinality / r, floored at 1e-9); log2 r; log2
+ * of the bytes of the inputs' run-length forms (summaries and containers)
+ * over their dense bytes, or 0 when an input has no run-length form.
  */
 int bm_query_features(const bm_pool* pool, const bm_query* q, float* out);
 
 /*
  * Install a trained selector: params (host fp32, the layout of
- * bm_mlp_forward with F = 5, H = 64, C = 5) predicts each candidate's log
+ * bm_mlp_forward with F = 6, H = 64, C = 6) predicts each candidate's log
  * time from the standardised features (x - mean) / std.  Queries with
  * path BM_PATH_AUTO then run the candidate with the smallest prediction
- * among those whose inputs are loaded.  params = NULL removes it (the fixed
- * density rule applies).  Results never depend on the choice.
+ * among those whose inputs are loaded (lists for ScanCount, run-length forms
+ * for candidate 5).  params = NULL removes it (the fixed density rule
+ * applies, with the run-length cost model).  Results never depend on the
+ * choice.
  */
 int bm_pool_set_selector(bm_pool* pool, const float* params, uint64_t nparams, const float* mean,
                          const float* stdev, uint32_t n_out);

@@ -268,11 +268,11 @@ def to_numpy_words(t: torch.Tensor) -> np.ndarray:
 
 KIND_THRESHOLD, KIND_INTERVAL, KIND_TABLE = 0, 1, 2
 PATH_AUTO, PATH_DENSE, PATH_SPARSE, PATH_RLE = 0, 1, 2, 3
-SELECTOR_FEATURES, SELECTOR_HIDDEN, SELECTOR_CANDIDATES = 5, 64, 5
+SELECTOR_FEATURES, SELECTOR_HIDDEN, SELECTOR_CANDIDATES = 6, 64, 6
 # candidate c of the selector: (path, sparse tile rows, or for the dense path
 # the words per thread: 0 = the pool's shape, 1 = one 64-bit word per thread)
 CANDIDATES = [(PATH_DENSE, 0), (PATH_SPARSE, 16384), (PATH_SPARSE, 32768), (PATH_SPARSE, 65536),
-              (PATH_DENSE, 1)]
+              (PATH_DENSE, 1), (PATH_RLE, 0)]
 
 
 def make_query(ids, kind: int = KIND_THRESHOLD, theta: int = 0, lo: int = 0, hi: int = 0,
@@ -411,7 +411,7 @@ def set_selector(pool: Pool, params: np.ndarray | None, mean=None, std=None) -> 
 # ---------------------------------------------------------------------------
 # selector network kernels (fp32, device tensors)
 
-def mlp_param_count(F: int = 5, H: int = 64, C: int = 5) -> int:
+def mlp_param_count(F: int = 6, H: int = 64, C: int = 6) -> int:
     return F * H + H + H * H + H + H * C + C
 
 

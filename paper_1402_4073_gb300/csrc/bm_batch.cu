@@ -12,6 +12,7 @@
 //    descriptor block, so the captured graph is replayed unchanged for every
 //    batch; only the block is copied to the device before each replay.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 
@@ -427,9 +428,10 @@ static int graph_for(bm_pool* p, BatchState* b, BatchSlot& sl, int K, uint32_t m
 #undef BM_BATCH_DISPATCH
 }
 
-// Learned choices for every AUTO query of a batch, on the device.
+// The learned selector's predictions for every AUTO query of a batch, on the
+// device: y[i * kCandidates + c].
 static int batch_select(bm_pool* p, BatchState* b, const std::vector<std::vector<float>>& feats,
-                        std::vector<int>& choice) {
+                        std::vector<float>& y) {
     const uint32_t B = (uint32_t)feats.size();
     if (!B) return BM_OK;
     const int F = kFeatures, H = kHidden, C = kCandidates;
@@ -447,7 +449,8 @@ static int batch_select(bm_pool* p, BatchState* b, const std::vector<std::vector
         if (rc) return rc;
         b->sel_cap = need;
     }
-    std::vector<float> x((size_t)B * F), y((size_t)B * C);
+    std::vector<float> x((size_t)B * F);
+    y.assign((size_t)B * C, 0.f);
     for (uint32_t i = 0; i < B; ++i)
         for (int f = 0; f < F; ++f) x[(size_t)i * F + f] = (feats[i][f] - p->sel_mean[f]) / p->sel_std[f];
     float* dP = b->d_sel;
@@ -461,13 +464,6 @@ static int batch_select(bm_pool* p, BatchState* b, const std::vector<std::vector
     if (rc) return rc;
     BM_CUDA_TRY(cudaMemcpyAsync(y.data(), dy, y.size() * 4, cudaMemcpyDeviceToHost, b->infer));
     BM_CUDA_TRY(cudaStreamSynchronize(b->infer));
-    choice.resize(B);
-    for (uint32_t i = 0; i < B; ++i) {
-        int best = 0;
-        for (int c = 1; c < C; ++c)
-            if (y[(size_t)i * C + c] < y[(size_t)i * C + best]) best = c;
-        choice[i] = best;
-    }
     return BM_OK;
 }
 
@@ -499,7 +495,7 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
         if (rc) return rc;
         total_ids += (qi.n + 3) & ~3u;  // each query's ids start 16-byte aligned
         if (qi.path == BM_PATH_AUTO) {
-            if (!p->sel_params.empty() && p->sel_outputs == kCandidates) {
+            if (selector_installed(p)) {
                 auto_idx.push_back(i);
                 feats.emplace_back(kFeatures);
                 query_features(p, qi.ids, qi.n, truth[i], feats.back().data());
@@ -512,21 +508,17 @@ extern "C" int bm_threshold_batch(bm_pool* p, const bm_query* q, uint32_t nq, ui
         }
     }
     if (!auto_idx.empty()) {
-        std::vector<int> choice;
-        int rc = batch_select(p, b, feats, choice);
+        std::vector<float> y;
+        int rc = batch_select(p, b, feats, y);
         if (rc) return rc;
+        // the smallest prediction among the candidates whose inputs are
+        // loaded; a query left in the batch's dense kernel shares the pool's
+        // reads with the others, so the dense predictions shrink by its gain
+        const float discount = (float)std::log(kBatchDenseSpeedup);
         for (size_t j = 0; j < auto_idx.size(); ++j) {
             const uint32_t i = auto_idx[j];
-            Candidate c = kCandidateTable[choice[j]];
-            // a candidate whose inputs are missing falls back to the one that exists
-            bool lists = true, dense = true;
-            for (uint32_t k = 0; k < q[i].n; ++k) {
-                lists = lists && p->list_present[q[i].ids[k]];
-                dense = dense && p->dense_present[q[i].ids[k]];
-            }
-            if (c.path == BM_PATH_SPARSE && !lists) c = kCandidateTable[0];
-            if (c.path == BM_PATH_DENSE && !dense) c = Candidate{BM_PATH_SPARSE, p->sparse_cfg.tile_rows, 0};
-            cand[i] = with_rle(p, q[i].ids, q[i].n, c, kBatchDenseSpeedup);
+            cand[i] = kCandidateTable[pick_candidate(p, q[i].ids, q[i].n,
+                                                     y.data() + j * kCandidates, discount)];
         }
     }
     std::vector<Pred> preds(nq);

@@ -10,7 +10,8 @@ const Candidate kCandidateTable[kCandidates] = {{BM_PATH_DENSE, 0, 0},
                                                 {BM_PATH_SPARSE, 16384, 0},
                                                 {BM_PATH_SPARSE, 32768, 0},
                                                 {BM_PATH_SPARSE, 65536, 0},
-                                                {BM_PATH_DENSE, 0, 1}};
+                                                {BM_PATH_DENSE, 0, 1},
+                                                {BM_PATH_RLE, 0, 0}};
 
 void query_features(const bm_pool* p, const uint32_t* ids, uint32_t n,
                     const std::vector<uint8_t>& f, float out[kFeatures]) {
@@ -31,12 +32,46 @@ void query_features(const bm_pool* p, const uint32_t* ids, uint32_t n,
     out[2] = (float)std::log10(std::max(sum / n, 1e-9));
     out[3] = (float)std::log10(std::max(mx, 1e-9));
     out[4] = (float)std::log2((double)p->r_bits);
+    // run-length forms: summaries (8 bytes per input and tile) and containers
+    bool rle = true;
+    uint64_t units = 0;
+    for (uint32_t k = 0; k < n && rle; ++k) {
+        rle = p->rle_present[ids[k]] != 0;
+        if (rle) units += p->rle_units[ids[k]];
+    }
+    const double tiles = (double)((p->words + kRleTileWords - 1) / kRleTileWords);
+    const double rle_bytes = 16.0 * (double)units + 8.0 * (double)n * tiles;
+    const double dense_bytes = (double)n * (double)p->r_bits / 8.0;
+    out[5] = rle ? (float)std::log2(std::max(rle_bytes, 1.0) / std::max(dense_bytes, 1.0)) : 0.f;
 }
 
 static bool all_have(const std::vector<uint8_t>& present, const uint32_t* ids, uint32_t n) {
     for (uint32_t k = 0; k < n; ++k)
         if (!present[ids[k]]) return false;
     return true;
+}
+
+int pick_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n, const float* y,
+                   float dense_discount) {
+    const bool lists = all_have(p->list_present, ids, n);
+    const bool dense = all_have(p->dense_present, ids, n);
+    const bool rle = all_have(p->rle_present, ids, n);
+    int best = -1, rle_c = -1;
+    for (int c = 0; c < kCandidates; ++c) {
+        const Candidate& k = kCandidateTable[c];
+        if (k.path == BM_PATH_RLE) {
+            if (rle) rle_c = c;
+            continue;
+        }
+        if ((k.path == BM_PATH_DENSE && !dense) || (k.path == BM_PATH_SPARSE && !lists)) continue;
+        if (best < 0 || y[c] < y[best]) best = c;
+    }
+    if (best < 0) return rle_c < 0 ? 0 : rle_c;
+    // the run-length path runs as a launch of its own: against a dense pick
+    // it must beat the dense prediction less the batch's discount
+    const float other =
+        y[best] - (kCandidateTable[best].path == BM_PATH_DENSE ? dense_discount : 0.f);
+    return rle_c >= 0 && y[rle_c] < other ? rle_c : best;
 }
 
 Candidate rule_choice(const bm_pool* p, const uint32_t* ids, uint32_t n) {
@@ -79,20 +114,12 @@ void mlp_forward_host(const float* P, int C, const float* x, float* y) {
 
 Candidate select_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
                            const std::vector<uint8_t>& f) {
-    if (p->sel_params.empty() || p->sel_outputs != kCandidates) return rule_choice(p, ids, n);
-    const bool lists = all_have(p->list_present, ids, n);
-    const bool dense = all_have(p->dense_present, ids, n);
+    if (!selector_installed(p)) return rule_choice(p, ids, n);
     float x[kFeatures], y[kCandidates];
     query_features(p, ids, n, f, x);
     for (int i = 0; i < kFeatures; ++i) x[i] = (x[i] - p->sel_mean[i]) / p->sel_std[i];
     mlp_forward_host(p->sel_params.data(), kCandidates, x, y);
-    int best = -1;
-    for (int c = 0; c < kCandidates; ++c) {
-        const Candidate& k = kCandidateTable[c];
-        if ((k.path == BM_PATH_DENSE && !dense) || (k.path == BM_PATH_SPARSE && !lists)) continue;
-        if (best < 0 || y[c] < y[best]) best = c;
-    }
-    return best < 0 ? kCandidateTable[0] : kCandidateTable[best];
+    return kCandidateTable[pick_candidate(p, ids, n, y, 0.f)];
 }
 
 // Cost of a single query on GB300 (device time with L2 flushed), fitted to
@@ -123,7 +150,8 @@ Candidate with_rle(const bm_pool* p, const uint32_t* ids, uint32_t n, Candidate 
 
 Candidate single_query_candidate(const bm_pool* p, const uint32_t* ids, uint32_t n,
                                  const std::vector<uint8_t>& f) {
-    return with_rle(p, ids, n, select_candidate(p, ids, n, f));
+    if (selector_installed(p)) return select_candidate(p, ids, n, f);
+    return with_rle(p, ids, n, rule_choice(p, ids, n));
 }
 
 }  // namespace bm

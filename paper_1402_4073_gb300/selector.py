@@ -1,13 +1,14 @@
 """Learned kernel selector: timing collection, training and evaluation.
 
-For every query the library can run one of five candidate kernels
+For every query the library can run one of six candidate kernels
 (``CANDIDATES``: the dense bit-sliced counter in the pool's shape, ScanCount
-with 16K, 32K or 64K-row tiles, or the dense counter with one 64-bit word per
-thread); results are identical, only the time differs.  The paper picks
-among its algorithms by measured time and scores each by its
-suboptimality, (t - t_best) / t_best (App. C).  Here a small network
-(5 -> 64 -> 64 -> 5, ReLU, fp32) predicts the log time of each candidate
-from the query's features; the smallest prediction wins.
+with 16K, 32K or 64K-row tiles, the dense counter with one 64-bit word per
+thread, or the run-length path); results are identical, only the time
+differs.  The paper picks among its algorithms by measured time and scores
+each by its suboptimality, (t - t_best) / t_best (App. C).  Here a small
+network (6 -> 64 -> 64 -> 6, ReLU, fp32) predicts the log time of each
+candidate from the query's features; the smallest prediction among the
+candidates the query's loaded forms allow wins.
 
 * ``collect``: time every candidate on every query with the library's own
   kernels (CUDA events around calls queued back to back) and read each
@@ -26,9 +27,10 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from . import (CANDIDATES, PATH_AUTO, PATH_DENSE, PATH_SPARSE, SELECTOR_CANDIDATES,
-               SELECTOR_FEATURES, SELECTOR_HIDDEN, Pool, PreparedQuery, mlp_adam, mlp_backward,
-               mlp_forward, mlp_param_count, query_features, query_select, set_selector)
+from . import (BM_ERANGE, CANDIDATES, PATH_AUTO, PATH_DENSE, PATH_RLE, PATH_SPARSE,
+               SELECTOR_CANDIDATES, SELECTOR_FEATURES, SELECTOR_HIDDEN, BMError, Pool,
+               PreparedQuery, mlp_adam, mlp_backward, mlp_forward, mlp_param_count,
+               query_features, query_select, set_selector)
 
 
 @dataclass
@@ -40,10 +42,11 @@ class Model:
 
 
 def collect(pool: Pool, queries, reps: int = 3, stream=None):
-    """(features [n, 5], times_us [n, 4]) for every query and candidate: the
+    """(features [n, F], times_us [n, C]) for every query and candidate: the
     device time per call, `reps` calls queued back to back behind a short
     sleep kernel (so that the host's own per-call time, the same for every
-    candidate, is not measured), mean per call."""
+    candidate, is not measured), mean per call.  A candidate the query's
+    loaded forms do not allow (no lists, no run-length forms) is NaN."""
     stream = stream or torch.cuda.current_stream()
     info = pool.info()
     feats = np.stack([query_features(pool, q) for q in queries]).astype(np.float32)
@@ -66,9 +69,16 @@ def collect(pool: Pool, queries, reps: int = 3, stream=None):
             if tile == 1:  # the one-word-per-thread shape, as the library runs candidate 4
                 d.update(variant=0, words_per_thread=1, adder=0 if d["adder"] == 2 else d["adder"])
             pool.set_dense_config(**d)
+        if path == PATH_RLE and info["rle_loaded"] == 0:
+            continue
         for i, q in enumerate(queries):
             pq = PreparedQuery(pool, q, out, path)
-            pq.run(card, stream)  # warm-up
+            try:
+                pq.run(card, stream)  # warm-up
+            except BMError as e:
+                if e.code != BM_ERANGE:  # only a missing form leaves the candidate out
+                    raise
+                continue
             with torch.cuda.stream(stream):
                 if sleep is not None:
                     sleep(100_000 * reps)  # about 50 us per call: the host queues the calls
@@ -99,10 +109,16 @@ def _init_params(seed: int) -> np.ndarray:
 
 def train(feats: np.ndarray, times_us: np.ndarray, steps: int = 3000, lr: float = 3e-3,
           seed: int = 1111, device: str = "cuda") -> Model:
-    """Fit log(time) per candidate with full-batch Adam on the GPU."""
-    ok = np.all(np.isfinite(times_us), axis=1)
+    """Fit log(time) per candidate with full-batch Adam on the GPU.  A
+    candidate a query cannot run (NaN time) is labelled ten times slower
+    than the query's slowest candidate that ran; it is never picked for such
+    a query anyway, since the selection skips candidates whose forms are
+    missing."""
+    ok = np.any(np.isfinite(times_us), axis=1)
     X = feats[ok].astype(np.float64)
     T = np.log(np.maximum(times_us[ok], 1e-3))
+    worst = np.nanmax(T, axis=1, keepdims=True) + np.log(10.0)
+    T = np.where(np.isfinite(T), T, worst)
     mean = X.mean(axis=0)
     std = X.std(axis=0)
     std[std < 1e-6] = 1.0
@@ -122,19 +138,23 @@ def train(feats: np.ndarray, times_us: np.ndarray, steps: int = 3000, lr: float 
 
 
 def predict(model: Model, feats: np.ndarray, device: str = "cuda") -> np.ndarray:
-    """Predicted log times [n, 4] by the library's forward kernel."""
+    """Predicted log times [n, C] by the library's forward kernel."""
     x = torch.from_numpy(((feats - model.mean) / model.std).astype(np.float32)).to(device)
     p = torch.from_numpy(model.params).to(device)
     y, _, _ = mlp_forward(p, x, SELECTOR_HIDDEN, SELECTOR_CANDIDATES)
     return y.cpu().numpy()
 
 
-def time_lost(times_us: np.ndarray, choice: np.ndarray) -> float:
-    """sum(t_chosen - t_best) / sum(t_best) over the queries with all times."""
-    ok = np.all(np.isfinite(times_us), axis=1)
+def time_lost(times_us: np.ndarray, choice: np.ndarray):
+    """sum(t_chosen - t_best) / sum(t_best) over the queries, t_best among the
+    candidates each query can run; None if a choice is one the query cannot
+    run (a fixed policy that some queries' forms do not allow)."""
+    ok = np.any(np.isfinite(times_us), axis=1)
     t = times_us[ok]
-    best = t.min(axis=1)
     chosen = t[np.arange(len(t)), choice[ok]]
+    if not np.all(np.isfinite(chosen)):
+        return None
+    best = np.nanmin(t, axis=1)
     return float((chosen - best).sum() / best.sum())
 
 
@@ -154,10 +174,12 @@ def installed_choices(pool: Pool, queries) -> np.ndarray:
     (the host-side inference that single queries use)."""
     tiles = {tile: c for c, (p, tile) in enumerate(CANDIDATES) if p == PATH_SPARSE}
     dense = {w: c for c, (p, w) in enumerate(CANDIDATES) if p == PATH_DENSE}
+    rle = CANDIDATES.index((PATH_RLE, 0))
     out = []
     for q in queries:
         path, tile = query_select(pool, q)
-        out.append(dense.get(tile, 0) if path == PATH_DENSE else tiles.get(tile, 2))
+        out.append(dense.get(tile, 0) if path == PATH_DENSE
+                   else rle if path == PATH_RLE else tiles.get(tile, 2))
     return np.array(out, dtype=np.int64)
 
 
@@ -167,7 +189,7 @@ def evaluate(pool: Pool, model: Model, queries, feats, times_us) -> dict:
     rule = rule_choices(pool, queries)
     install(pool, model)
     mlp_choice = installed_choices(pool, queries)
-    ok = np.all(np.isfinite(times_us), axis=1)
+    ok = np.any(np.isfinite(times_us), axis=1)
     res = {"queries": int(ok.sum()),
            "time_lost_mlp": time_lost(times_us, mlp_choice),
            "time_lost_rule": time_lost(times_us, rule),
@@ -178,6 +200,7 @@ def evaluate(pool: Pool, model: Model, queries, feats, times_us) -> dict:
     res["total_us_best"] = best_total
     res["total_us_mlp"] = best_total * (1 + res["time_lost_mlp"])
     res["total_us_rule"] = best_total * (1 + res["time_lost_rule"])
+    res["mlp_choices"] = np.bincount(mlp_choice[ok], minlength=SELECTOR_CANDIDATES).tolist()
     return res
 
 

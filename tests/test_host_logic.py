@@ -56,8 +56,11 @@ def test_time_lost_metric():
     worst = np.array([0, 3, 3])
     # (10-5) + (4-1) + (8-1) over 5+1+1
     assert abs(selector.time_lost(times, worst) - 15.0 / 7.0) < 1e-12
-    times[1, 2] = np.nan  # incomplete rows are left out
-    assert abs(selector.time_lost(times, worst) - 12.0 / 6.0) < 1e-12
+    # a NaN is a candidate the query cannot run: its row stays, its best is
+    # among the others, and a policy choosing it has no time lost
+    times[1, 0] = np.nan
+    assert abs(selector.time_lost(times, worst) - 14.0 / 8.0) < 1e-12
+    assert selector.time_lost(times, np.array([1, 0, 2])) is None
 
 
 def test_serving_summary():
