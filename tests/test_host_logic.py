@@ -48,6 +48,32 @@ def test_floyd_and_queries(dg):
     assert np.all(np.diff(t) > 0) and abs(len(sv) / t[-1] - 1000.0) < 200.0
 
 
+def test_clustered_workload(dg):
+    """Five blocks of ids with runs of growing mean length: the mean length
+    of the runs of ones grows block by block; every query stays inside one
+    block, blocks in turn, and its predicate is in range."""
+    r, n = 1 << 18, 50
+    words, flat, offs, d = dg.clustered_pool(n, r)
+    assert words.shape == (n, (r + 63) // 64) and len(offs) == n + 1
+    bits = np.unpackbits(words.view(np.uint8), axis=1, bitorder="little")[:, :r].astype(np.int8)
+    ones = bits.sum(axis=1)
+    starts = np.maximum(np.diff(bits, axis=1), 0).sum(axis=1) + bits[:, 0]
+    assert np.array_equal(offs[1:] - offs[:-1], ones.astype(np.uint64))
+    per = n // len(dg.CLUSTERED_RUNS)
+    mean_run = [ones[g * per:(g + 1) * per].sum() / max(1, starts[g * per:(g + 1) * per].sum())
+                for g in range(len(dg.CLUSTERED_RUNS))]
+    assert all(a < b for a, b in zip(mean_run, mean_run[1:])), mean_run
+    assert np.all((d >= 1e-4) & (d <= 0.5))
+    qs = dg.clustered_queries(40, n, nmax=n)
+    for i, q in enumerate(qs):
+        g = i % len(dg.CLUSTERED_RUNS)
+        assert np.all(q.ids // per == g) and len(set(q.ids.tolist())) == len(q.ids)
+        if q.kind == dg.KIND_INTERVAL:
+            assert 1 <= q.lo <= q.hi <= len(q.ids)
+        else:
+            assert 1 <= q.theta <= min(len(q.ids), 64)
+
+
 def test_time_lost_metric():
     from paper_1402_4073_gb300 import selector
     times = np.array([[10.0, 5.0, 7.0, 9.0], [1.0, 2.0, 3.0, 4.0], [4.0, 4.0, 1.0, 8.0]])
