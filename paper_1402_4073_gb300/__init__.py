@@ -38,8 +38,15 @@ def check(rc: int, what: str = "") -> None:
         raise BMError(rc, what)
 
 
+# the current stream's raw handle without building a Stream object (a few
+# microseconds per call otherwise, as much as a small query's kernel)
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream(stream) -> int:
     if stream is None:
+        if _raw_stream is not None:
+            return int(_raw_stream(torch.cuda.current_device()))
         return torch.cuda.current_stream().cuda_stream
     if isinstance(stream, torch.cuda.Stream):
         return stream.cuda_stream
